@@ -1,0 +1,95 @@
+"""Workload definitions and seeded synthetic inputs.
+
+This module is shared by the tests, the benchmark and the smoke check.  It
+holds parameter tables and random-input recipes only: none of the method's
+arithmetic.  It imports neither the CUDA binding nor the oracle.
+
+The disk parameters are the paper's Benchmark table (gas surface density and
+temperature at 1 AU, alpha, v_frag, erosion mass ratio, p, q); everything the
+paper does not give (dust-to-gas ratio, radial extent, monomer size and
+density, stellar mass, molecular constants, grouping and fragment-slope
+parameters) is a stated reading.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+AU = 1.495978707e13  # cm
+YR = 3.15576e7       # s (Julian year)
+
+# relative-velocity term switches and transport switches (shared numbering)
+DV_ALL = 31
+TR_RADIAL, TR_VERTICAL, TR_ST_MIDPLANE = 1, 2, 4
+
+
+def benchmark_disk(**over) -> dict:
+    """The paper's Benchmark-table disk (CGS), with the readings filled in."""
+    d = dict(
+        sigma0=1000.0, p=1.0, T0=280.0, q=0.5, alpha=1e-3, v_frag=1000.0, erosion_ratio=10.0,
+        dust_to_gas=0.01, r_in=1.0 * AU, r_out=100.0 * AU, m_star=1.0, rho_s=1.6, a_mono=1e-4,
+        mu=2.34, sigma_h2=2e-15, dm_group=1e-3, frag_xi=11.0 / 6.0, erosion_chi=1.0,
+        K_const=1.0, V_const=1.0, m_init=0.0, M_total=0.0,
+        kernel_mode=0, settle_form=0, dv_flags=DV_ALL, tr_flags=TR_RADIAL | TR_VERTICAL,
+    )
+    d.update(over)
+    return d
+
+
+def constant_kernel_cell(**over) -> dict:
+    """0D well-mixed cell, constant kernel K = 1, V = 1, monomers of mass 1,
+    total mass 1 (so the initial monomer number density is 1)."""
+    d = benchmark_disk(kernel_mode=1, K_const=1.0, V_const=1.0, m_init=1.0, M_total=1.0, dm_group=0.0,
+                       tr_flags=0)
+    d.update(over)
+    return d
+
+
+# ---- the five workloads -------------------------------------------------
+WORKLOADS = {
+    "0d_const_200": dict(params=constant_kernel_cell(), n_r=1, n_z=1, per_cell=200, t_end=100.0, seed=0),
+    "disk2d_16x4x100": dict(params=benchmark_disk(), n_r=16, n_z=4, per_cell=100, t_end=1e4 * YR, seed=0),
+    "disk2d_256x16x200": dict(params=benchmark_disk(), n_r=256, n_z=16, per_cell=200, t_end=1e4 * YR, seed=0),
+    "stress_1024x32x400": dict(params=benchmark_disk(alpha=1e-2, v_frag=100.0), n_r=1024, n_z=32, per_cell=400,
+                               t_end=1e3 * YR, seed=0),
+}
+
+
+def batched_disks(n_disks: int = 64, key=(2507, 0xB47C)):
+    """64 independent disks: alpha in {1e-4,1e-3,1e-2}, v_frag in {1,3,10,30} m/s,
+    radial zones uniform in 32..512 and particles per cell uniform in 50..400
+    (drawn from numpy's Philox with the stated key), 8 vertical cells."""
+    rng = np.random.Generator(np.random.Philox(key=list(key)))
+    alphas = (1e-4, 1e-3, 1e-2)
+    vfr = (100.0, 300.0, 1000.0, 3000.0)
+    n_r = rng.integers(32, 513, size=n_disks)
+    ppc = rng.integers(50, 401, size=n_disks)
+    disks = []
+    for d in range(n_disks):
+        disks.append(dict(params=benchmark_disk(alpha=alphas[d % 3], v_frag=vfr[(d // 3) % 4]),
+                          n_r=int(n_r[d]), n_z=8, per_cell=int(ppc[d]), seed=d))
+    return disks
+
+
+# ---- random inputs for the unit-level parity tests ----------------------
+def random_masses(n: int, seed: int, lo: float = 1e-12, hi: float = 1e4, ties: float = 0.1) -> np.ndarray:
+    """Log-uniform masses over [lo, hi] with a fraction of exact repeats and of
+    near-repeats (relative offsets 1e-9..1e-3), so that equal and nearly equal
+    pairs occur."""
+    rng = np.random.default_rng(seed)
+    m = np.exp(rng.uniform(np.log(lo), np.log(hi), n))
+    k = int(ties * n)
+    if k and n > 2:
+        src = rng.integers(0, n, k)
+        dst = rng.integers(0, n, k)
+        m[dst] = m[src]
+        dst2 = rng.integers(0, n, k)
+        m[dst2] = m[rng.integers(0, n, k)] * (1.0 + np.exp(rng.uniform(np.log(1e-9), np.log(1e-3), k)))
+    return m
+
+
+def random_cell_positions(n: int, seed: int, params: dict) -> tuple[np.ndarray, np.ndarray]:
+    """Random (r, z) inside the disk; z scaled by a rough aspect ratio 0.05 r."""
+    rng = np.random.default_rng(seed)
+    r = rng.uniform(params["r_in"], params["r_out"], n)
+    z = rng.normal(0.0, 1.0, n) * 0.05 * r
+    return r, z
