@@ -1,0 +1,242 @@
+/*
+ * mcd.h -- C ABI of libmcd.so, a GB300 (sm_103a) implementation of the hot
+ * path of mcdust (Vaikundaraman, Gurrutxaga & Drazkowska 2025, "mcdust: A 2D
+ * Monte Carlo code for dust coagulation in protoplanetary disks").
+ *
+ * The path, per time step (Summary section): particles binned into an
+ * adaptive grid whose cells hold equal numbers of representative particles
+ * (mcd_regrid); in every cell, the representative-particle Monte Carlo
+ * collision chain of Zsom & Dullemond (2008) with sticking, fragmentation and
+ * erosion outcomes (mcd_collide); then radial and vertical transport of the
+ * particles in a static, vertically isothermal power-law gas disk
+ * (mcd_transport).  mcd_step runs the three in that order.
+ *
+ * Conventions for every call:
+ *  - CGS units; times in seconds.
+ *  - Every call returns an int: MCD_OK (0) or a negative MCD_E* code.  No C++
+ *    exception crosses this boundary.  Device-side failures (NaN positions,
+ *    an event-count cap reached) latch into a status word that mcd_sync and
+ *    mcd_get_stats return.
+ *  - Work is enqueued on the CUDA stream given to mcd_init_disk and calls
+ *    return without waiting, except those that copy to host memory
+ *    (mcd_get_*, mcd_sync), which synchronise that stream.
+ *  - The caller owns the device workspace (its size from mcd_workspace_size)
+ *    and every host array passed in; the library owns the context and never
+ *    allocates device memory after mcd_init_disk.
+ *  - Disks are independent: arrays of n_disks parameter sets and grids run
+ *    together in one set of launches.
+ */
+#ifndef MCD_H
+#define MCD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define MCD_OK 0
+#define MCD_EINVAL -1   /* invalid argument (sizes, pointers, parameters) */
+#define MCD_ENOMEM -2   /* workspace smaller than mcd_workspace_size */
+#define MCD_ECUDA -3    /* a CUDA runtime call failed */
+#define MCD_ENAN -4     /* NaN met in particle positions */
+#define MCD_ETIMEOUT -5 /* a cell reached the per-call event cap */
+#define MCD_EEMPTY -6   /* every particle of a disk has been removed */
+#define MCD_ESTATE -7   /* call out of order (e.g. collide before regrid) */
+
+/* ---- precision of the collision arithmetic ------------------------------ */
+#define MCD_FP64 0  /* everything in FP64 */
+#define MCD_MIXED 1 /* dv, sigma, K and rates in FP32; masses, clock and the
+                       running row sums in FP64 / compensated FP32 */
+
+/* ---- where a pointer lives ---------------------------------------------- */
+#define MCD_HOST 0
+#define MCD_DEVICE 1
+
+/* ---- switches ------------------------------------------------------------ */
+#define MCD_DV_BM 1    /* Brownian motion */
+#define MCD_DV_TURB 2  /* turbulence (Ormel & Cuzzi 2007 closed forms) */
+#define MCD_DV_RAD 4   /* radial drift */
+#define MCD_DV_PHI 8   /* azimuthal drift */
+#define MCD_DV_SET 16  /* vertical settling */
+#define MCD_TR_RADIAL 1
+#define MCD_TR_VERTICAL 2
+#define MCD_TR_ST_MIDPLANE 4 /* transport uses the midplane Stokes number */
+
+/*
+ * One disk.  The first seven fields are the paper's Benchmark table (gas
+ * surface density and temperature at 1 AU, alpha, v_frag, erosion mass ratio,
+ * p, q).  The rest are not given by the paper and are readings: dust-to-gas
+ * ratio, radial extent, stellar mass [M_sun], monomer density and radius,
+ * mean molecular weight, H2 cross-section, the Zsom & Dullemond grouping
+ * ratio dm_group (0 = off), the fragment mass slope frag_xi (n(m) ~ m^-xi),
+ * the eroded-mass factor erosion_chi, and overrides for the 0D
+ * constant-kernel test problem (kernel_mode = 1: K = K_const, V = V_const,
+ * always sticking).  m_init > 0 overrides the monomer mass, M_total > 0 the
+ * disk dust mass.  settle_form 0: v_z = -z Omega St; 1: -z Omega St/(1+St).
+ */
+typedef struct {
+    double sigma0, p, T0, q, alpha, v_frag, erosion_ratio;
+    double dust_to_gas, r_in, r_out, m_star, rho_s, a_mono;
+    double mu, sigma_h2, dm_group, frag_xi, erosion_chi;
+    double K_const, V_const, m_init, M_total;
+    int32_t kernel_mode, settle_form, dv_flags, tr_flags;
+} mcd_disk_params;
+
+/* n_r radial zones x n_z cells per zone, per_cell particles per cell at start */
+typedef struct {
+    int32_t n_r, n_z, per_cell, reserved;
+} mcd_grid;
+
+typedef struct {
+    double t;             /* clock [s] */
+    int64_t step;         /* steps (transport calls) taken */
+    int64_t events;       /* collision events, cumulative */
+    int64_t n_alive;      /* particles not yet removed at r_in */
+    double accreted_mass; /* swarm mass removed at r_in [g] */
+    int32_t status;       /* latched device status, an MCD_* code */
+    int32_t reserved;
+} mcd_stats;
+
+typedef struct mcd_ctx mcd_ctx;
+
+/* ---- options (mcd_set_option) -------------------------------------------- */
+#define MCD_OPT_MAX_EVENTS 1    /* per cell per collide call; reaching it latches MCD_ETIMEOUT (default 1e7) */
+#define MCD_OPT_CAP_STOPS 2     /* 1: reaching MAX_EVENTS stops the cell without an error (tests) */
+#define MCD_OPT_REBUILD_EVERY 3 /* events between full row-sum rebuilds; 0 = n of the cell (default) */
+#define MCD_OPT_USE_GRAPH 4     /* 1: mcd_step replays a captured CUDA graph (default 1) */
+#define MCD_OPT_DUMP_R 5        /* 1: keep each particle's row sum after collide (mcd_get_rates) */
+#define MCD_OPT_LOG_CELL 6      /* global cell index whose events are logged; -1 off (default) */
+#define MCD_OPT_LPT 7           /* 1: order cells by descending work estimate (default 1) */
+#define MCD_OPT_THREADS 8       /* threads per cell in collide; 0 = auto */
+
+/*
+ * Bytes of device workspace needed for n_disks disks at precision prec.
+ * p[n_disks], g[n_disks] host arrays.  Returns MCD_EINVAL on a bad grid.
+ */
+int mcd_workspace_size(const mcd_disk_params *p, const mcd_grid *g, int32_t n_disks, int32_t prec, size_t *bytes);
+
+/*
+ * Create a context and the initial particles (workload recipe of the paper's
+ * Benchmark: equal swarm masses summing to the disk's dust mass, r drawn from
+ * the dust-mass distribution, z ~ N(0, H_g(r)), monomers), then bin them
+ * (mcd_regrid).  Random numbers come from Philox4x64-10 keyed by (seed, disk).
+ * device_workspace: caller-owned device memory of ws_bytes >= the size from
+ * mcd_workspace_size, 256-byte aligned; it must outlive the context.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ */
+int mcd_init_disk(mcd_ctx **out, const mcd_disk_params *p, const mcd_grid *g, int32_t n_disks, uint64_t seed,
+                  int32_t prec, void *device_workspace, size_t ws_bytes, void *cuda_stream);
+
+/*
+ * Advance every cell's clock to t_end with the representative-particle
+ * event chain (Summary: sticking, fragmentation, erosion; Zsom & Dullemond
+ * 2008): waiting times from the total rate, partner selection by rate
+ * weight, only row and column i of the rate matrix updated per event.
+ * Requires current cells (mcd_regrid after the last transport).
+ */
+int mcd_collide(mcd_ctx *ctx, double t_end);
+
+/*
+ * Move every particle over dt (Summary: transport in the radial and vertical
+ * directions): radial drift plus turbulent diffusion, settling plus mixing.
+ * Particles crossing r_in are removed (their swarm mass is accreted); those
+ * crossing r_out are reflected.  Increments the step counter.
+ */
+int mcd_transport(mcd_ctx *ctx, double dt);
+
+/*
+ * Re-bin particles into equal-count cells (Summary: adaptive grid): n_r
+ * radial zones of equal count by (r, id), then n_z cells of equal count per
+ * zone by (z, id); particle arrays are reordered into cell order.
+ */
+int mcd_regrid(mcd_ctx *ctx);
+
+/* One step: regrid, collide to t + dt, transport dt (dt > 0). */
+int mcd_step(mcd_ctx *ctx, double dt);
+
+/*
+ * Copy disk `disk`'s particles in cell order (dead ones, r = +inf, last).
+ * Arrays of at least the disk's initial particle count; any may be NULL.
+ * where = MCD_HOST (synchronises) or MCD_DEVICE (device pointers, async).
+ */
+int mcd_get_particles(mcd_ctx *ctx, int32_t disk, double *m, double *M, double *r, double *z, uint32_t *id,
+                      int64_t *count, int32_t where);
+
+/*
+ * Replace disk `disk`'s particles (count must equal its initial particle
+ * count; ids a permutation of 0..count-1; r = +inf marks a removed particle).
+ * Cells become stale: call mcd_regrid before mcd_collide.
+ */
+int mcd_set_particles(mcd_ctx *ctx, int32_t disk, const double *m, const double *M, const double *r,
+                      const double *z, const uint32_t *id, int64_t count, int32_t where);
+
+/*
+ * Cells of disk `disk` after the last regrid: cell_off[n_r*n_z+1] particle
+ * offsets within the disk, bounds[6 per cell] = r_lo r_hi z_lo z_hi r_c z_c,
+ * V[n_r*n_z] volumes.  Any pointer may be NULL.
+ */
+int mcd_get_cells(mcd_ctx *ctx, int32_t disk, int64_t *cell_off, double *bounds, double *V, int32_t where);
+
+/* Per-particle row sums R_i after the last collide (needs MCD_OPT_DUMP_R). */
+int mcd_get_rates(mcd_ctx *ctx, int32_t disk, double *R, int32_t where);
+
+/* Per-cell event counts of the last collide, n_r*n_z entries. */
+int mcd_get_cell_events(mcd_ctx *ctx, int32_t disk, int64_t *events, int32_t where);
+
+/*
+ * Event log of the cell chosen with MCD_OPT_LOG_CELL: up to cap records of
+ * (i, j, outcome) as int32 triples and the event time t and new mass of i.
+ * outcome 0 stick, 1 fragment, 2 erode.  Returns the number logged in *n.
+ */
+int mcd_get_event_log(mcd_ctx *ctx, int32_t *ijo, double *t, double *m_new, int64_t cap, int64_t *n);
+
+int mcd_get_stats(mcd_ctx *ctx, int32_t disk, mcd_stats *out);
+int mcd_set_option(mcd_ctx *ctx, int32_t key, double value);
+
+/*
+ * Phase tracing.  With on = 1 every later mcd_step records CUDA events on the
+ * context's stream before the regrid, after the regrid, after the cell
+ * ordering, after the collisions and after the transport (inside the step's
+ * CUDA graph when graphs are on).  mcd_trace_read waits for the last traced
+ * step and writes its four phase durations [regrid, order, collide,
+ * transport] in milliseconds to ms[4].
+ */
+int mcd_trace(mcd_ctx *ctx, int32_t on);
+int mcd_trace_read(mcd_ctx *ctx, float *ms);
+
+/* Number of kernels this context has launched so far (graph replays count
+   every kernel node). */
+int mcd_get_launch_count(mcd_ctx *ctx, int64_t *launches);
+
+/* Synchronise the context's stream; returns the latched device status. */
+int mcd_sync(mcd_ctx *ctx);
+
+/* Release the context (not the caller's workspace). */
+int mcd_free(mcd_ctx *ctx);
+
+const char *mcd_strerror(int code);
+
+/*
+ * Pair probe (parity tests): relative velocity and collision kernel of n
+ * pairs (m_i[k], m_j[k]) in the gas at cell centre (r_c, z_c), computed by
+ * the device functions the collide kernel uses, at precision prec.
+ * m_i, m_j, dv, K: device arrays of n doubles.  Asynchronous on stream.
+ */
+int mcd_pair_probe(const mcd_disk_params *p, int32_t prec, double r_c, double z_c, int64_t n, const double *m_i,
+                   const double *m_j, double *dv, double *K, void *cuda_stream);
+
+/*
+ * Rate-matrix probe: rate[i*n+j] = K_ij (M_j/V) min(1/m_j, 1/(dm m_i)) and
+ * the row sums R[i] of one cell of n <= 1024 swarms, computed by the collide
+ * kernel's build phase at precision prec.  Device arrays; asynchronous.
+ */
+int mcd_rate_probe(const mcd_disk_params *p, int32_t prec, double r_c, double z_c, double V, int32_t n,
+                   const double *m, const double *M, double *rate, double *R, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCD_H */

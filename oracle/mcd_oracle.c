@@ -336,14 +336,16 @@ void orc_rate_matrix(const orc_params *P, double rc, double zc, double V, int64_
     }
 }
 
-/* mass-weighted fragment draw on [m0, mmax] from n(m) ~ m^-xi */
+/* mass-weighted fragment draw on [m0, mmax] from n(m) ~ m^-xi: the inverse of
+   the CDF (m^e - m0^e)/(mmax^e - m0^e), e = 2 - xi, written as
+   m = m0 [1 + u ((mmax/m0)^e - 1)]^(1/e) with expm1/log1p so that it keeps
+   its relative precision when mmax is close to m0 */
 static double orc_fragment(const orc_params *P, double m0, double mmax, double u)
 {
     if (mmax <= m0) return m0;
-    double e = 2.0 - P->frag_xi;
-    if (fabs(e) < 1e-12) return m0 * exp(u * log(mmax / m0));
-    double lo = pow(m0, e), hi = pow(mmax, e);
-    return pow(lo + u * (hi - lo), 1.0 / e);
+    double e = 2.0 - P->frag_xi, L = log(mmax / m0);
+    if (fabs(e) < 1e-12) return m0 * exp(u * L);
+    return m0 * exp(log1p(u * expm1(e * L)) / e);
 }
 
 double orc_fragment_probe(const orc_params *P, double m0, double mmax, double u) { return orc_fragment(P, m0, mmax, u); }

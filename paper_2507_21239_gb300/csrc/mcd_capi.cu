@@ -1,0 +1,591 @@
+// mcd_capi.cu -- the C ABI of libmcd.so (declared in include/mcd.h): context,
+// workspace carving, argument checks, the step sequence and its CUDA graph.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "mcd_internal.cuh"
+
+
+using namespace mcd;
+
+namespace {
+
+constexpr int64_t kZoneCap = 14336;  // (z, id, src) triples of one radial zone in shared memory
+
+struct Carver {
+    char *base;
+    size_t off = 0;
+    explicit Carver(void *b) : base((char *)b) {}
+    template <class T>
+    T *take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+struct Sizes {
+    int64_t N = 0, C = 0, Z = 0, T = 0;
+    int32_t n_max = 0;
+    std::vector<DiskDev> disks;
+};
+
+int plan(const mcd_disk_params *p, const mcd_grid *g, int32_t nd, Sizes &S)
+{
+    if (!p || !g || nd <= 0) return MCD_EINVAL;
+    S.disks.resize(nd);
+    for (int d = 0; d < nd; ++d) {
+        const mcd_grid &G = g[d];
+        const mcd_disk_params &P = p[d];
+        if (G.n_r <= 0 || G.n_z <= 0 || G.per_cell <= 0) return MCD_EINVAL;
+        if (G.per_cell > kMaxCell) return MCD_EINVAL;
+        if ((int64_t)G.n_z * G.per_cell > kZoneCap) return MCD_EINVAL;
+        if (P.kernel_mode == 1) {
+            if (!(P.V_const > 0.0) || !(P.m_init > 0.0)) return MCD_EINVAL;
+        } else if (P.kernel_mode == 0) {
+            if (!(P.r_in > 0.0) || !(P.r_out > P.r_in) || !(P.rho_s > 0.0) || !(P.a_mono > 0.0 || P.m_init > 0.0) ||
+                !(P.m_star > 0.0) || !(P.mu > 0.0) || !(P.sigma_h2 > 0.0) || !(P.sigma0 > 0.0) || !(P.T0 > 0.0) ||
+                !(P.alpha > 0.0) || !(P.dm_group >= 0.0) || !(P.frag_xi < 2.0 + 1e-12 || P.frag_xi > 2.0))
+                return MCD_EINVAL;
+        } else {
+            return MCD_EINVAL;
+        }
+        DiskDev &D = S.disks[d];
+        D.n_r = G.n_r;
+        D.n_z = G.n_z;
+        D.n0 = (int64_t)G.n_r * G.n_z * G.per_cell;
+        D.p_off = S.N;
+        D.c_off = S.C;
+        D.z_off = S.Z;
+        D.t_off = S.T;
+        D.n_tiles = (D.n0 + kRadixTile - 1) / kRadixTile;
+        S.N += D.n0;
+        S.C += (int64_t)G.n_r * G.n_z;
+        S.Z += G.n_r;
+        S.T += D.n_tiles;
+        if (G.per_cell > S.n_max) S.n_max = G.per_cell;
+    }
+    if (S.N >= ((int64_t)1 << 31)) return MCD_EINVAL;
+    return MCD_OK;
+}
+
+size_t carve(mcd_ctx *c, void *base, const Sizes &S, int32_t nd)
+{
+    Carver cv(base);
+    mcd_ctx tmp;
+    mcd_ctx *x = c ? c : &tmp;
+    x->d_params = cv.take<mcd_disk_params>(nd);
+    x->d_disks = cv.take<DiskDev>(nd);
+    x->slot_disk = cv.take<int32_t>(S.N);
+    x->cell_disk = cv.take<int32_t>(S.C);
+    x->zone_disk = cv.take<int32_t>(S.Z);
+    x->tile_disk = cv.take<int32_t>(S.T);
+    for (int b = 0; b < 2; ++b) {
+        x->m[b] = cv.take<double>(S.N);
+        x->M[b] = cv.take<double>(S.N);
+        x->r[b] = cv.take<double>(S.N);
+        x->z[b] = cv.take<double>(S.N);
+        x->id[b] = cv.take<uint32_t>(S.N);
+        x->key[b] = cv.take<uint64_t>(S.N);
+        x->val[b] = cv.take<uint32_t>(S.N);
+    }
+    int64_t H = 256 * S.T;
+    x->hist = cv.take<uint32_t>(H);
+    x->scan_part = cv.take<uint32_t>(H / 4096 + 2);
+    x->cell_start = cv.take<int64_t>(S.C);
+    x->cell_n = cv.take<int32_t>(S.C);
+    x->cell_b = cv.take<double>(6 * S.C);
+    x->cell_V = cv.take<double>(S.C);
+    x->cell_events = cv.take<int64_t>(S.C);
+    x->cell_cost = cv.take<uint32_t>(S.C);
+    x->queue = cv.take<int32_t>(S.C);
+    x->qcount = cv.take<int32_t>(72);
+    x->n_alive = cv.take<int64_t>(nd);
+    x->accreted = cv.take<double>(nd);
+    x->events_total = cv.take<unsigned long long>(nd);
+    x->Rdump = cv.take<double>(S.N);
+    x->log_ijo = cv.take<int32_t>(3 * mcd_ctx::kLogCap);
+    x->log_t = cv.take<double>(mcd_ctx::kLogCap);
+    x->log_m = cv.take<double>(mcd_ctx::kLogCap);
+    x->log_n = cv.take<unsigned long long>(1);
+    x->status = cv.take<int32_t>(1);
+    x->state = cv.take<StepState>(1);
+    x->d_Mswarm = cv.take<double>(nd);
+    return (cv.off + 255) & ~(size_t)255;
+}
+
+double disk_dust_mass(const mcd_disk_params &P)
+{
+    if (P.M_total > 0.0) return P.M_total;
+    double e = 2.0 - P.p, ri = P.r_in / kAU, ro = P.r_out / kAU;
+    double I = fabs(e) < 1e-12 ? log(ro / ri) : (pow(ro, e) - pow(ri, e)) / e;
+    return P.dust_to_gas * 2.0 * kPI * P.sigma0 * I * kAU * kAU;
+}
+
+int cuda_code(cudaError_t e) { return e == cudaSuccess ? MCD_OK : MCD_ECUDA; }
+
+int status_code(int32_t st)
+{
+    if (st & kStNaN) return MCD_ENAN;
+    if (st & kStBadCell) return MCD_EINVAL;
+    if (st & kStTimeout) return MCD_ETIMEOUT;
+    if (st & kStEmpty) return MCD_EEMPTY;
+    return MCD_OK;
+}
+
+void drop_graphs(mcd_ctx *c)
+{
+    for (int k = 0; k < 2; ++k)
+        if (c->gexec[k]) {
+            cudaGraphExecDestroy(c->gexec[k]);
+            c->gexec[k] = nullptr;
+        }
+}
+
+cudaError_t enqueue_regrid(mcd_ctx *c)
+{
+    cudaError_t e = launch_regrid(c);
+    c->cur ^= 1;
+    return e;
+}
+
+cudaError_t mark(mcd_ctx *c, int k)
+{
+    return c->trace ? cudaEventRecordWithFlags(c->tev[k], c->stream, cudaEventRecordExternal) : cudaSuccess;
+}
+
+cudaError_t enqueue_step_body(mcd_ctx *c)
+{
+    cudaError_t e = mark(c, 0);
+    if (e == cudaSuccess) e = enqueue_regrid(c);
+    if (e == cudaSuccess) e = mark(c, 1);
+    if (e == cudaSuccess && c->lpt) e = launch_lpt(c);
+    if (e == cudaSuccess) e = mark(c, 2);
+    if (e == cudaSuccess) e = launch_collide_impl(c, 1, 0.0);
+    if (e == cudaSuccess) e = mark(c, 3);
+    if (e == cudaSuccess) e = launch_transport(c);
+    if (e == cudaSuccess) e = launch_advance_clock(c, 1);
+    if (e == cudaSuccess) e = mark(c, 4);
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mcd_workspace_size(const mcd_disk_params *p, const mcd_grid *g, int32_t n_disks, int32_t prec, size_t *bytes)
+{
+    if (!bytes || (prec != MCD_FP64 && prec != MCD_MIXED)) return MCD_EINVAL;
+    Sizes S;
+    int rc = plan(p, g, n_disks, S);
+    if (rc) return rc;
+    *bytes = carve(nullptr, nullptr, S, n_disks);
+    return MCD_OK;
+}
+
+int mcd_init_disk(mcd_ctx **out, const mcd_disk_params *p, const mcd_grid *g, int32_t n_disks, uint64_t seed,
+                  int32_t prec, void *ws, size_t ws_bytes, void *stream)
+{
+    if (!out || !ws || (prec != MCD_FP64 && prec != MCD_MIXED)) return MCD_EINVAL;
+    if (((uintptr_t)ws & 255) != 0) return MCD_EINVAL;
+    *out = nullptr;
+    Sizes S;
+    int rc = plan(p, g, n_disks, S);
+    if (rc) return rc;
+    size_t need = carve(nullptr, nullptr, S, n_disks);
+    if (ws_bytes < need) return MCD_ENOMEM;
+    mcd_ctx *c = new (std::nothrow) mcd_ctx();
+    if (!c) return MCD_ENOMEM;
+    c->n_disks = n_disks;
+    c->prec = prec;
+    c->stream = (cudaStream_t)stream;
+    c->seed = seed;
+    c->hp.assign(p, p + n_disks);
+    c->hg.assign(g, g + n_disks);
+    c->hd = S.disks;
+    c->N = S.N;
+    c->C = S.C;
+    c->Z = S.Z;
+    c->n_tiles = S.T;
+    c->n_max = S.n_max;
+    carve(c, ws, S, n_disks);
+    double *d_Mswarm = c->d_Mswarm;
+
+    // host-built tables
+    std::vector<int32_t> cell_disk(S.C), zone_disk(S.Z), tile_disk(S.T), slot_disk(S.N);
+    std::vector<double> Msw(n_disks);
+    for (int d = 0; d < n_disks; ++d) {
+        const DiskDev &D = S.disks[d];
+        for (int64_t k = 0; k < (int64_t)D.n_r * D.n_z; ++k) cell_disk[D.c_off + k] = d;
+        for (int64_t k = 0; k < D.n_r; ++k) zone_disk[D.z_off + k] = d;
+        for (int64_t k = 0; k < D.n_tiles; ++k) tile_disk[D.t_off + k] = d;
+        for (int64_t k = 0; k < D.n0; ++k) slot_disk[D.p_off + k] = d;
+        Msw[d] = disk_dust_mass(p[d]) / (double)D.n0;
+    }
+    cudaStream_t st = c->stream;
+    cudaError_t e = cudaSuccess;
+    auto cp = [&](void *dst, const void *src, size_t n) {
+        if (e == cudaSuccess && n) e = cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, st);
+    };
+    cp(c->d_params, p, sizeof(mcd_disk_params) * n_disks);
+    cp(c->d_disks, S.disks.data(), sizeof(DiskDev) * n_disks);
+    cp(c->cell_disk, cell_disk.data(), 4 * S.C);
+    cp(c->zone_disk, zone_disk.data(), 4 * S.Z);
+    cp(c->tile_disk, tile_disk.data(), 4 * S.T);
+    cp(c->slot_disk, slot_disk.data(), 4 * S.N);
+    cp(d_Mswarm, Msw.data(), 8 * n_disks);
+    StepState s0 = {0.0, 0.0, 0};
+    cp(c->state, &s0, sizeof s0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->accreted, 0, 8 * n_disks, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->events_total, 0, 8 * n_disks, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->cell_events, 0, 8 * S.C, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->log_n, 0, 8, st);
+    if (e == cudaSuccess) e = prepare_collide(c);
+    if (e == cudaSuccess) e = prepare_zone(c);
+    if (e == cudaSuccess) e = launch_init(c, d_Mswarm);
+    if (e == cudaSuccess) e = enqueue_regrid(c);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        delete c;
+        return MCD_ECUDA;
+    }
+    c->cells_valid = true;
+    *out = c;
+    return MCD_OK;
+}
+
+int mcd_regrid(mcd_ctx *c)
+{
+    if (!c) return MCD_EINVAL;
+    int rc = cuda_code(enqueue_regrid(c));
+    if (rc == MCD_OK) c->cells_valid = true;
+    return rc;
+}
+
+int mcd_collide(mcd_ctx *c, double t_end)
+{
+    if (!c || !(t_end >= c->t_host)) return MCD_EINVAL;
+    if (!c->cells_valid) return MCD_ESTATE;
+    cudaError_t e = cudaSuccess;
+    if (c->lpt) e = launch_lpt(c);
+    if (e == cudaSuccess) e = launch_collide_impl(c, 0, t_end);
+    if (e == cudaSuccess) e = launch_set_clock(c, t_end, 1, 0.0, 0);
+    if (e == cudaSuccess) c->t_host = t_end;
+    return cuda_code(e);
+}
+
+int mcd_transport(mcd_ctx *c, double dt)
+{
+    if (!c || !(dt > 0.0) || !isfinite(dt)) return MCD_EINVAL;
+    cudaError_t e = launch_set_clock(c, 0.0, 0, dt, 1);
+    if (e == cudaSuccess) e = launch_transport(c);
+    if (e == cudaSuccess) e = launch_advance_clock(c, 0);
+    if (e == cudaSuccess) {
+        c->step_host += 1;
+        c->cells_valid = false;
+    }
+    return cuda_code(e);
+}
+
+int mcd_step(mcd_ctx *c, double dt)
+{
+    if (!c || !(dt > 0.0) || !isfinite(dt)) return MCD_EINVAL;
+    cudaError_t e = launch_set_clock(c, 0.0, 0, dt, 1);
+    if (e != cudaSuccess) return MCD_ECUDA;
+    if (c->use_graph) {
+        int p = c->cur;
+        if (!c->gexec[p]) {
+            // capture on a private stream (capture is illegal on the legacy
+            // default stream); the graph is then launched on the caller's stream
+            if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+                return MCD_ECUDA;
+            cudaGraph_t gr = nullptr;
+            const int64_t l0 = c->launches;
+            cudaStream_t user = c->stream;
+            c->stream = c->cap_stream;
+            e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) {
+                c->stream = user;
+                return MCD_ECUDA;
+            }
+            cudaError_t eb = enqueue_step_body(c);
+            e = cudaStreamEndCapture(c->stream, &gr);
+            c->stream = user;
+            c->cur = p;  // the capture only recorded; the state did not change
+            c->graph_launches[p] = c->launches - l0;
+            c->launches = l0;
+            if (eb != cudaSuccess || e != cudaSuccess) {
+                if (gr) cudaGraphDestroy(gr);
+                return MCD_ECUDA;
+            }
+            e = cudaGraphInstantiate(&c->gexec[p], gr, 0);
+            cudaGraphDestroy(gr);
+            if (e != cudaSuccess) {
+                c->gexec[p] = nullptr;
+                return MCD_ECUDA;
+            }
+        }
+        e = cudaGraphLaunch(c->gexec[p], c->stream);
+        if (e != cudaSuccess) return MCD_ECUDA;
+        c->launches += c->graph_launches[p];
+        c->cur = p ^ 1;
+    } else {
+        e = enqueue_step_body(c);
+        if (e != cudaSuccess) return MCD_ECUDA;
+    }
+    c->t_host += dt;
+    c->step_host += 1;
+    c->cells_valid = false;
+    return MCD_OK;
+}
+
+int mcd_get_particles(mcd_ctx *c, int32_t disk, double *m, double *M, double *r, double *z, uint32_t *id,
+                      int64_t *count, int32_t where)
+{
+    if (!c || disk < 0 || disk >= c->n_disks || (where != MCD_HOST && where != MCD_DEVICE)) return MCD_EINVAL;
+    const DiskDev &D = c->hd[disk];
+    const int b = c->cur;
+    cudaMemcpyKind kind = where == MCD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    cudaError_t e = cudaSuccess;
+    auto cp = [&](void *dst, const void *src, size_t n) {
+        if (dst && e == cudaSuccess) e = cudaMemcpyAsync(dst, src, n, kind, c->stream);
+    };
+    cp(m, c->m[b] + D.p_off, 8 * D.n0);
+    cp(M, c->M[b] + D.p_off, 8 * D.n0);
+    cp(r, c->r[b] + D.p_off, 8 * D.n0);
+    cp(z, c->z[b] + D.p_off, 8 * D.n0);
+    cp(id, c->id[b] + D.p_off, 4 * D.n0);
+    if (count) *count = D.n0;
+    if (e == cudaSuccess && where == MCD_HOST) e = cudaStreamSynchronize(c->stream);
+    return cuda_code(e);
+}
+
+int mcd_set_particles(mcd_ctx *c, int32_t disk, const double *m, const double *M, const double *r, const double *z,
+                      const uint32_t *id, int64_t count, int32_t where)
+{
+    if (!c || disk < 0 || disk >= c->n_disks || (where != MCD_HOST && where != MCD_DEVICE)) return MCD_EINVAL;
+    const DiskDev &D = c->hd[disk];
+    if (count != D.n0 || !m || !M || !r || !z || !id) return MCD_EINVAL;
+    if (where == MCD_HOST) {
+        std::vector<char> seen(D.n0, 0);
+        for (int64_t k = 0; k < D.n0; ++k) {
+            if ((int64_t)id[k] >= D.n0 || seen[id[k]]) return MCD_EINVAL;
+            seen[id[k]] = 1;
+        }
+    }
+    const int b = c->cur;
+    cudaMemcpyKind kind = where == MCD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    cudaError_t e = cudaSuccess;
+    auto cp = [&](void *dst, const void *src, size_t n) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, n, kind, c->stream);
+    };
+    cp(c->m[b] + D.p_off, m, 8 * D.n0);
+    cp(c->M[b] + D.p_off, M, 8 * D.n0);
+    cp(c->r[b] + D.p_off, r, 8 * D.n0);
+    cp(c->z[b] + D.p_off, z, 8 * D.n0);
+    cp(c->id[b] + D.p_off, id, 4 * D.n0);
+    if (e == cudaSuccess && where == MCD_HOST) e = cudaStreamSynchronize(c->stream);
+    c->cells_valid = false;
+    return cuda_code(e);
+}
+
+int mcd_get_cells(mcd_ctx *c, int32_t disk, int64_t *cell_off, double *bounds, double *V, int32_t where)
+{
+    if (!c || disk < 0 || disk >= c->n_disks || where != MCD_HOST) return MCD_EINVAL;
+    const DiskDev &D = c->hd[disk];
+    int64_t nc = (int64_t)D.n_r * D.n_z;
+    std::vector<int64_t> start(nc);
+    std::vector<int32_t> n(nc);
+    cudaError_t e = cudaMemcpyAsync(start.data(), c->cell_start + D.c_off, 8 * nc, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(n.data(), c->cell_n + D.c_off, 4 * nc, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && bounds)
+        e = cudaMemcpyAsync(bounds, c->cell_b + 6 * D.c_off, 48 * nc, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && V) e = cudaMemcpyAsync(V, c->cell_V + D.c_off, 8 * nc, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return MCD_ECUDA;
+    if (cell_off) {
+        for (int64_t k = 0; k < nc; ++k) cell_off[k] = start[k] - D.p_off;
+        cell_off[nc] = nc ? cell_off[nc - 1] + n[nc - 1] : 0;
+    }
+    return MCD_OK;
+}
+
+int mcd_get_rates(mcd_ctx *c, int32_t disk, double *R, int32_t where)
+{
+    if (!c || disk < 0 || disk >= c->n_disks || !R || (where != MCD_HOST && where != MCD_DEVICE)) return MCD_EINVAL;
+    const DiskDev &D = c->hd[disk];
+    cudaError_t e = cudaMemcpyAsync(R, c->Rdump + D.p_off, 8 * D.n0,
+                                    where == MCD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess && where == MCD_HOST) e = cudaStreamSynchronize(c->stream);
+    return cuda_code(e);
+}
+
+int mcd_get_cell_events(mcd_ctx *c, int32_t disk, int64_t *events, int32_t where)
+{
+    if (!c || disk < 0 || disk >= c->n_disks || !events || (where != MCD_HOST && where != MCD_DEVICE))
+        return MCD_EINVAL;
+    const DiskDev &D = c->hd[disk];
+    cudaError_t e = cudaMemcpyAsync(events, c->cell_events + D.c_off, 8 * (int64_t)D.n_r * D.n_z,
+                                    where == MCD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess && where == MCD_HOST) e = cudaStreamSynchronize(c->stream);
+    return cuda_code(e);
+}
+
+int mcd_get_event_log(mcd_ctx *c, int32_t *ijo, double *t, double *m_new, int64_t cap, int64_t *n)
+{
+    if (!c || !n || cap < 0) return MCD_EINVAL;
+    unsigned long long ln = 0;
+    cudaError_t e = cudaMemcpyAsync(&ln, c->log_n, 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return MCD_ECUDA;
+    int64_t k = (int64_t)ln < cap ? (int64_t)ln : cap;
+    if (k > 0) {
+        if (ijo) e = cudaMemcpyAsync(ijo, c->log_ijo, 12 * k, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess && t) e = cudaMemcpyAsync(t, c->log_t, 8 * k, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess && m_new) e = cudaMemcpyAsync(m_new, c->log_m, 8 * k, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    *n = (int64_t)ln;
+    return cuda_code(e);
+}
+
+int mcd_get_stats(mcd_ctx *c, int32_t disk, mcd_stats *out)
+{
+    if (!c || !out || disk < 0 || disk >= c->n_disks) return MCD_EINVAL;
+    int64_t na = 0;
+    double acc = 0.0;
+    unsigned long long ev = 0;
+    int32_t st = 0;
+    StepState s;
+    cudaError_t e = cudaMemcpyAsync(&na, c->n_alive + disk, 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&acc, c->accreted + disk, 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ev, c->events_total + disk, 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st, c->status, 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&s, c->state, sizeof s, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return MCD_ECUDA;
+    out->t = s.t;
+    out->step = s.step;
+    out->events = (int64_t)ev;
+    out->n_alive = na;
+    out->accreted_mass = acc;
+    out->status = status_code(st);
+    out->reserved = 0;
+    return MCD_OK;
+}
+
+int mcd_set_option(mcd_ctx *c, int32_t key, double v)
+{
+    if (!c) return MCD_EINVAL;
+    switch (key) {
+    case MCD_OPT_MAX_EVENTS:
+        if (!(v >= 0)) return MCD_EINVAL;
+        c->max_events = (int64_t)v;
+        break;
+    case MCD_OPT_CAP_STOPS: c->cap_stops = v != 0.0; break;
+    case MCD_OPT_REBUILD_EVERY:
+        if (!(v >= 0)) return MCD_EINVAL;
+        c->rebuild_every = (int64_t)v;
+        break;
+    case MCD_OPT_USE_GRAPH: c->use_graph = v != 0.0; break;
+    case MCD_OPT_DUMP_R: c->dump_R = v != 0.0; break;
+    case MCD_OPT_LOG_CELL: c->log_cell = (int64_t)v; break;
+    case MCD_OPT_LPT: c->lpt = v != 0.0; break;
+    case MCD_OPT_THREADS:
+        if (v != 0.0 && (v < c->n_max || v > kMaxCell || ((int)v % 32) != 0)) return MCD_EINVAL;
+        c->threads = (int32_t)v;
+        break;
+    default: return MCD_EINVAL;
+    }
+    drop_graphs(c);
+    return MCD_OK;
+}
+
+int mcd_trace(mcd_ctx *c, int32_t on)
+{
+    if (!c) return MCD_EINVAL;
+    if (on && !c->tev[0])
+        for (int k = 0; k < 5; ++k)
+            if (cudaEventCreate(&c->tev[k]) != cudaSuccess) return MCD_ECUDA;
+    c->trace = on ? 1 : 0;
+    drop_graphs(c);
+    return MCD_OK;
+}
+
+int mcd_trace_read(mcd_ctx *c, float *ms)
+{
+    if (!c || !ms || !c->tev[0]) return MCD_EINVAL;
+    if (cudaEventSynchronize(c->tev[4]) != cudaSuccess) return MCD_ECUDA;
+    for (int k = 0; k < 4; ++k)
+        if (cudaEventElapsedTime(&ms[k], c->tev[k], c->tev[k + 1]) != cudaSuccess) return MCD_ECUDA;
+    return MCD_OK;
+}
+
+int mcd_get_launch_count(mcd_ctx *c, int64_t *launches)
+{
+    if (!c || !launches) return MCD_EINVAL;
+    *launches = c->launches;
+    return MCD_OK;
+}
+
+int mcd_sync(mcd_ctx *c)
+{
+    if (!c) return MCD_EINVAL;
+    int32_t st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, c->status, 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return MCD_ECUDA;
+    return status_code(st);
+}
+
+int mcd_free(mcd_ctx *c)
+{
+    if (!c) return MCD_EINVAL;
+    cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    for (int k = 0; k < 5; ++k)
+        if (c->tev[k]) cudaEventDestroy(c->tev[k]);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+    return MCD_OK;
+}
+
+const char *mcd_strerror(int code)
+{
+    switch (code) {
+    case MCD_OK: return "ok";
+    case MCD_EINVAL: return "invalid argument";
+    case MCD_ENOMEM: return "workspace too small";
+    case MCD_ECUDA: return "CUDA runtime error";
+    case MCD_ENAN: return "NaN in particle positions";
+    case MCD_ETIMEOUT: return "a cell reached the event cap";
+    case MCD_EEMPTY: return "every particle of a disk was removed";
+    case MCD_ESTATE: return "call out of order";
+    default: return "unknown status";
+    }
+}
+
+int mcd_pair_probe(const mcd_disk_params *p, int32_t prec, double rc, double zc, int64_t n, const double *mi,
+                   const double *mj, double *dv, double *K, void *stream)
+{
+    if (!p || n < 0 || (n > 0 && (!mi || !mj || !dv || !K)) || (prec != MCD_FP64 && prec != MCD_MIXED))
+        return MCD_EINVAL;
+    return cuda_code(launch_pair_probe(*p, prec, rc, zc, n, mi, mj, dv, K, (cudaStream_t)stream));
+}
+
+int mcd_rate_probe(const mcd_disk_params *p, int32_t prec, double rc, double zc, double V, int32_t n,
+                   const double *m, const double *M, double *rate, double *R, void *stream)
+{
+    if (!p || n < 0 || n > 1024 || (n > 0 && (!m || !M || !rate || !R)) || (prec != MCD_FP64 && prec != MCD_MIXED))
+        return MCD_EINVAL;
+    return cuda_code(launch_rate_probe(*p, prec, rc, zc, V, n, m, M, rate, R, (cudaStream_t)stream));
+}
+
+}  // extern "C"

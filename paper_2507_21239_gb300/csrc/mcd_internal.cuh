@@ -1,0 +1,235 @@
+// mcd_internal.cuh -- shared device helpers and the host context of libmcd.
+//
+// Physics follows the Summary section of the mcdust paper (static power-law,
+// vertically isothermal gas disk; Epstein/Stokes drag; relative velocities
+// from Brownian motion, turbulence, radial and azimuthal drift and settling;
+// Zsom & Dullemond representative particles).  The paper prints no formulas:
+// each form here is the standard published one, the same reading as the
+// project's written design.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "mcd.h"
+
+namespace mcd {
+
+// ---- constants (CGS) -------------------------------------------------------
+constexpr double kGMsun = 1.32712440018e26;  // G M_sun [cm^3 s^-2]
+constexpr double kAU = 1.495978707e13;       // [cm]
+constexpr double kKB = 1.380649e-16;         // [erg/K]
+constexpr double kMP = 1.67262192e-24;       // [g]
+constexpr double kPI = 3.141592653589793;
+constexpr double kYA = 1.6;                  // Ormel & Cuzzi (2007) y_a
+
+constexpr uint64_t kTagInit = 1, kTagCollide = 2, kTagTransport = 3;
+
+// status bits latched on the device (mapped to MCD_* codes on the host)
+constexpr int kStNaN = 1, kStTimeout = 2, kStEmpty = 4, kStBadCell = 8;
+
+// ---- Philox4x64-10 (Salmon et al., SC'11) ---------------------------------
+struct U4 {
+    uint64_t x[4];
+};
+
+__host__ __device__ inline void mulhilo(uint64_t a, uint64_t b, uint64_t &hi, uint64_t &lo)
+{
+#if defined(__CUDA_ARCH__)
+    hi = __umul64hi(a, b);
+    lo = a * b;
+#else
+    unsigned __int128 p = (unsigned __int128)a * b;
+    hi = (uint64_t)(p >> 64);
+    lo = (uint64_t)p;
+#endif
+}
+
+__host__ __device__ inline U4 philox(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3, uint64_t k0,
+                                     uint64_t k1)
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint64_t h0, l0, h1, l1;
+        mulhilo(M0, c0, h0, l0);
+        mulhilo(M1, c2, h1, l1);
+        uint64_t n0 = h1 ^ c1 ^ k0, n2 = h0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = l1;
+        c2 = n2;
+        c3 = l0;
+        k0 += W0;
+        k1 += W1;
+    }
+    U4 o;
+    o.x[0] = c0;
+    o.x[1] = c1;
+    o.x[2] = c2;
+    o.x[3] = c3;
+    return o;
+}
+
+// (0,1) from the top 53 bits; the float version rounds that same 53-bit value
+// (relative precision 2^-24 at every magnitude, so log u stays accurate near 0)
+__host__ __device__ inline double u01d(uint64_t x) { return ((double)(x >> 11) + 0.5) * 0x1.0p-53; }
+__host__ __device__ inline float u01f(uint64_t x) { return ((float)(x >> 11) + 0.5f) * 0x1.0p-53f; }
+
+// ---- gas disk at (r, z) ------------------------------------------------------
+template <class T>
+struct Gas {
+    T Sigma, T_, cs, Omega, H, rho, vth, lambda, nu, etavk, D, vg2, St_eta, asw;
+};
+
+__device__ inline double mpow(double x, double y) { return pow(x, y); }
+__device__ inline float mpow(float x, float y) { return powf(x, y); }
+__device__ inline double mexp(double x) { return exp(x); }
+__device__ inline float mexp(float x) { return expf(x); }
+__device__ inline double msqrt(double x) { return sqrt(x); }
+__device__ inline float msqrt(float x) { return sqrtf(x); }
+__device__ inline double mcbrt(double x) { return cbrt(x); }
+__device__ inline float mcbrt(float x) { return cbrtf(x); }
+__device__ inline double mlog(double x) { return log(x); }
+__device__ inline float mlog(float x) { return logf(x); }
+__device__ inline double mexpm1(double x) { return expm1(x); }
+__device__ inline float mexpm1(float x) { return expm1f(x); }
+
+// all quantities of the static power-law, vertically isothermal disk
+template <class T>
+__device__ inline Gas<T> gas_at(const mcd_disk_params &P, double r, double z)
+{
+    Gas<T> g;
+    T x = (T)r * (T)(1.0 / kAU);
+    T rr = (T)r, zz = (T)z;
+    g.Sigma = (T)P.sigma0 * mpow(x, -(T)P.p);
+    g.T_ = (T)P.T0 * mpow(x, -(T)P.q);
+    g.cs = msqrt((T)kKB * g.T_ / ((T)P.mu * (T)kMP));
+    g.Omega = msqrt((T)(P.m_star * kGMsun) / rr / rr / rr);
+    g.H = g.cs / g.Omega;
+    T rho_mid = g.Sigma / ((T)2.5066282746310002 * g.H);  // sqrt(2 pi)
+    T s = zz / g.H;
+    g.rho = rho_mid * mexp((T)-0.5 * s * s);
+    g.vth = (T)1.5957691216057308 * g.cs;  // sqrt(8/pi)
+    g.lambda = ((T)P.mu * (T)kMP / (T)P.sigma_h2) / g.rho;
+    g.nu = (T)0.5 * g.vth * g.lambda;
+    g.etavk = (T)0.5 * g.cs * g.cs / (g.Omega * rr) * ((T)P.p + (T)0.5 * ((T)3 + (T)P.q));
+    g.D = (T)P.alpha * g.cs * g.H;
+    g.vg2 = (T)1.5 * (T)P.alpha * g.cs * g.cs;
+    g.St_eta = (T)1 / msqrt(g.D / g.nu);
+    g.asw = (T)2.25 * g.lambda;
+    return g;
+}
+
+__host__ __device__ inline double monomer_mass(const mcd_disk_params &P)
+{
+    return P.m_init > 0.0 ? P.m_init : 4.0 * kPI / 3.0 * P.rho_s * P.a_mono * P.a_mono * P.a_mono;
+}
+
+// ---- per-disk tables ---------------------------------------------------------
+struct DiskDev {
+    int64_t p_off, n0;       // particle slots [p_off, p_off + n0)
+    int64_t c_off;           // first global cell
+    int64_t z_off;           // first global radial zone
+    int64_t t_off, n_tiles;  // radix tiles
+    int32_t n_r, n_z;
+};
+
+struct StepState {
+    double t, dt;
+    int64_t step;
+};
+
+// radix sort tile: 256 threads x 16 keys
+constexpr int kRadixThreads = 256, kRadixItems = 16, kRadixTile = kRadixThreads * kRadixItems;
+constexpr int kRadixBins = 256, kRadixPasses = 8;
+
+// largest cell population the collide kernel takes (one thread per swarm)
+constexpr int kMaxCell = 512;
+
+}  // namespace mcd
+
+// ---- host context ------------------------------------------------------------
+struct mcd_ctx {
+    int32_t n_disks = 0, prec = 0;
+    cudaStream_t stream = nullptr;
+    uint64_t seed = 0;
+    std::vector<mcd_disk_params> hp;
+    std::vector<mcd_grid> hg;
+    std::vector<mcd::DiskDev> hd;
+    int64_t N = 0, C = 0, Z = 0, n_tiles = 0;
+    int32_t n_max = 0;  // largest possible cell population
+
+    mcd_disk_params *d_params = nullptr;
+    mcd::DiskDev *d_disks = nullptr;
+    int32_t *slot_disk = nullptr;  // disk of each particle slot [N]
+    int32_t *cell_disk = nullptr;  // disk of each global cell [C]
+    int32_t *zone_disk = nullptr;  // disk of each global zone [Z]
+    int32_t *tile_disk = nullptr;  // disk of each radix tile [n_tiles]
+
+    double *m[2] = {}, *M[2] = {}, *r[2] = {}, *z[2] = {};
+    uint32_t *id[2] = {};
+    int cur = 0;
+
+    uint64_t *key[2] = {};
+    uint32_t *val[2] = {};
+    uint32_t *hist = nullptr;      // [n_tiles * 256] in (disk, digit, tile) order
+    uint32_t *scan_part = nullptr; // block partials of the histogram scan
+
+    int64_t *cell_start = nullptr;  // global particle slot of each cell's first particle
+    int32_t *cell_n = nullptr;
+    double *cell_b = nullptr;  // 6 per cell: r_lo r_hi z_lo z_hi r_c z_c
+    double *cell_V = nullptr;
+
+    int64_t *cell_events = nullptr;
+    uint32_t *cell_cost = nullptr;
+    int32_t *queue = nullptr;
+    int32_t *qcount = nullptr;  // [64 bins + head]
+    int64_t *n_alive = nullptr;
+    double *accreted = nullptr;
+    unsigned long long *events_total = nullptr;
+    double *Rdump = nullptr;
+    int32_t *log_ijo = nullptr;
+    double *log_t = nullptr, *log_m = nullptr;
+    unsigned long long *log_n = nullptr;
+    int32_t *status = nullptr;
+    mcd::StepState *state = nullptr;
+    double *d_Mswarm = nullptr;  // per-disk initial swarm mass
+    static constexpr int64_t kLogCap = 1 << 16;
+
+    // options
+    int64_t max_events = 10000000;  // per cell per collide call; bounds every event loop
+    int32_t cap_stops = 0;
+    int64_t rebuild_every = 0;
+    int32_t use_graph = 1, dump_R = 0, lpt = 1, threads = 0;
+    int64_t log_cell = -1;
+
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int64_t graph_launches[2] = {0, 0};  // kernels per replay of each graph
+    int64_t launches = 0;                // kernels launched so far
+    int32_t trace = 0;
+    cudaEvent_t tev[5] = {};
+    cudaStream_t cap_stream = nullptr;  // private stream the step graph is captured on
+    bool cells_valid = false;
+    double t_host = 0.0;
+    int64_t step_host = 0;
+};
+
+// ---- launchers (defined across the translation units) ----------------------------
+namespace mcd {
+cudaError_t launch_init(mcd_ctx *c, const double *d_Mswarm);
+cudaError_t launch_transport(mcd_ctx *c);  // reads dt and step from the device state
+cudaError_t launch_regrid(mcd_ctx *c);     // gathers into buffer 1 - cur; caller flips cur
+cudaError_t launch_lpt(mcd_ctx *c);
+cudaError_t launch_collide_impl(mcd_ctx *c, int t_end_from_state, double t_end);
+cudaError_t launch_set_clock(mcd_ctx *c, double t, int set_t, double dt, int set_dt);
+cudaError_t launch_advance_clock(mcd_ctx *c, int add_dt_to_t);
+cudaError_t prepare_collide(mcd_ctx *c);
+cudaError_t prepare_zone(mcd_ctx *c);
+cudaError_t launch_pair_probe(const mcd_disk_params &p, int prec, double rc, double zc, int64_t n,
+                              const double *mi, const double *mj, double *dv, double *K, cudaStream_t s);
+cudaError_t launch_rate_probe(const mcd_disk_params &p, int prec, double rc, double zc, double V, int n,
+                              const double *m, const double *M, double *rate, double *R, cudaStream_t s);
+}  // namespace mcd

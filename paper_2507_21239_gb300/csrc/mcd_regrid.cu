@@ -1,0 +1,457 @@
+// mcd_regrid.cu -- the adaptive equal-count grid (Summary of the mcdust paper:
+// "each cell has equal number of representative particles").
+//
+// Rule (reading): particles are ranked by (r, id); radial zone k of n_r takes
+// the next floor(N/n_r) of them, the first N mod n_r zones one extra; within a
+// zone particles are ranked by (z, id) and split into n_z cells the same way.
+// Interior cell edges are midpoints of neighbouring sorted positions, outer
+// edges extend by half the first / last spacing, V = pi (r_hi^2 - r_lo^2)
+// (z_hi - z_lo).  Removed particles (r = +inf) stay at the tail in id order.
+//
+// GB300 design:
+//  1. keys: each particle's order-preserving 64-bit r key is written at
+//     position (disk offset + id), so a stable sort by r alone breaks ties by id;
+//  2. a segmented LSD radix sort, 8 passes of 8 bits, all disks in one launch
+//     sequence (tiles never straddle disks; the histogram is laid out disk-major,
+//     digit, tile so one exclusive scan yields every scatter offset);
+//  3. one CTA per radial zone loads its (z, id) keys into shared memory, sorts
+//     them with a bitonic network that needs no padding (every compare is
+//     ascending, absent elements act as +inf), computes cell bounds with
+//     explicitly rounded FP64 operations (no fused multiply-add, so they are
+//     bit-identical to a plain CPU evaluation), and gathers the particle
+//     columns into cell order.
+#include <math.h>
+
+#include "mcd_internal.cuh"
+
+namespace mcd {
+
+__device__ __forceinline__ uint64_t order_key(double x)
+{
+    if (x == 0.0) x = 0.0;  // -0.0 -> +0.0
+    uint64_t b = (uint64_t)__double_as_longlong(x);
+    return (b & 0x8000000000000000ULL) ? ~b : (b | 0x8000000000000000ULL);
+}
+
+__device__ __forceinline__ double key_value(uint64_t k)
+{
+    uint64_t b = (k & 0x8000000000000000ULL) ? (k & 0x7FFFFFFFFFFFFFFFULL) : ~k;
+    return __longlong_as_double((long long)b);
+}
+
+constexpr uint64_t kInfKey = 0xFFF0000000000000ULL;  // order_key(+inf)
+
+__global__ void k_regrid_keys(const DiskDev *disks, const int32_t *slot_disk, int64_t N, const double *r,
+                              const double *z, const uint32_t *id, uint64_t *key, uint32_t *val, int32_t *status)
+{
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    int d = slot_disk[s];
+    double rs = r[s];
+    if (isnan(rs) || isnan(z[s])) {
+        atomicOr(status, kStNaN);
+        rs = INFINITY;
+    }
+    uint32_t k = id[s];
+    if ((int64_t)k >= disks[d].n0) {
+        atomicOr(status, kStBadCell);
+        return;
+    }
+    int64_t dst = disks[d].p_off + k;
+    key[dst] = order_key(rs);
+    val[dst] = (uint32_t)(s - disks[d].p_off);
+}
+
+// histogram index of (tile t of disk d, digit b)
+__device__ __forceinline__ int64_t hidx(const DiskDev &D, int64_t t, int b)
+{
+    return 256 * D.t_off + (int64_t)b * D.n_tiles + (t - D.t_off);
+}
+
+__global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const DiskDev *disks, const int32_t *tile_disk,
+                                                              const uint64_t *key, int shift, uint32_t *hist)
+{
+    __shared__ uint32_t h[kRadixBins];
+    int64_t t = blockIdx.x;
+    const DiskDev D = disks[tile_disk[t]];
+    int64_t start = D.p_off + (t - D.t_off) * kRadixTile;
+    int64_t end = min(start + kRadixTile, D.p_off + D.n0);
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t q = start + threadIdx.x; q < end; q += kRadixThreads) atomicAdd(&h[(key[q] >> shift) & 255], 1u);
+    __syncthreads();
+    hist[hidx(D, t, threadIdx.x)] = h[threadIdx.x];
+}
+
+constexpr int kScanThreads = 1024, kScanItems = 4, kScanBlock = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t x, uint32_t *wsum, uint32_t &total)
+{
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t v = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) wsum[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t s = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) wsum[lane] = s;
+    }
+    __syncthreads();
+    total = wsum[nw - 1];
+    uint32_t res = v - x + (w > 0 ? wsum[w - 1] : 0);
+    __syncthreads();
+    return res;
+}
+
+// exclusive scan of each block of kScanBlock entries in place; block totals to part
+__global__ void __launch_bounds__(kScanThreads) k_scan_blocks(uint32_t *a, int64_t n, uint32_t *part)
+{
+    __shared__ uint32_t wsum[32];
+    int64_t base = blockIdx.x * (int64_t)kScanBlock + threadIdx.x * kScanItems;
+    uint32_t v[kScanItems], s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = base + i < n ? a[base + i] : 0;
+        s += v[i];
+    }
+    uint32_t tot;
+    uint32_t ex = block_excl_scan_u32(s, wsum, tot);
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < n) a[base + i] = ex;
+        ex += v[i];
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+// exclusive scan of the block totals (one CTA, any length)
+__global__ void __launch_bounds__(kScanThreads) k_scan_parts(uint32_t *part, int64_t n)
+{
+    __shared__ uint32_t wsum[32];
+    uint32_t carry = 0;
+    for (int64_t base = 0; base < n; base += kScanThreads) {
+        int64_t q = base + threadIdx.x;
+        uint32_t x = q < n ? part[q] : 0, tot;
+        uint32_t ex = block_excl_scan_u32(x, wsum, tot);
+        if (q < n) part[q] = ex + carry;
+        carry += tot;
+    }
+}
+
+__global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const DiskDev *disks, const int32_t *tile_disk,
+                                                                 const uint64_t *ksrc, const uint32_t *vsrc,
+                                                                 uint64_t *kdst, uint32_t *vdst, int shift,
+                                                                 const uint32_t *hist, const uint32_t *part)
+{
+    __shared__ uint32_t wcnt[kRadixThreads / 32][kRadixBins];
+    __shared__ uint32_t toff[kRadixBins];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t t = blockIdx.x;
+    const DiskDev D = disks[tile_disk[t]];
+    int64_t start = D.p_off + (t - D.t_off) * kRadixTile;
+    int64_t end = min(start + kRadixTile, D.p_off + D.n0);
+    {
+        int64_t hi = hidx(D, t, threadIdx.x);
+        toff[threadIdx.x] = hist[hi] + part[hi / kScanBlock];
+    }
+    for (int q = threadIdx.x; q < (kRadixThreads / 32) * kRadixBins; q += kRadixThreads) (&wcnt[0][0])[q] = 0;
+    __syncthreads();
+    uint64_t kk[kRadixItems];
+    uint32_t vv[kRadixItems], rk[kRadixItems];
+    int dg[kRadixItems];
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int it = 0; it < kRadixItems; ++it) {
+        int64_t q = start + (int64_t)w * (32 * kRadixItems) + it * 32 + lane;
+        bool ok = q < end;
+        kk[it] = ok ? ksrc[q] : 0;
+        vv[it] = ok ? vsrc[q] : 0;
+        int digit = ok ? (int)((kk[it] >> shift) & 255) : 256;
+        dg[it] = digit;
+        unsigned peers = __match_any_sync(0xffffffffu, digit);
+        int leader = __ffs(peers) - 1;
+        uint32_t old = 0;
+        if (lane == leader && ok) {
+            old = wcnt[w][digit];
+            wcnt[w][digit] = old + __popc(peers);
+        }
+        old = __shfl_sync(0xffffffffu, old, leader);
+        rk[it] = old + __popc(peers & lt);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        int b = threadIdx.x;
+        uint32_t run = 0;
+#pragma unroll
+        for (int ww = 0; ww < kRadixThreads / 32; ++ww) {
+            uint32_t c = wcnt[ww][b];
+            wcnt[ww][b] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kRadixItems; ++it) {
+        if (dg[it] < 256) {
+            uint32_t pos = toff[dg[it]] + wcnt[w][dg[it]] + rk[it];
+            kdst[pos] = kk[it];
+            vdst[pos] = vv[it];
+        }
+    }
+}
+
+__global__ void k_count_alive(const DiskDev *disks, int nd, const uint64_t *key, int64_t *n_alive, int32_t *status)
+{
+    int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= nd) return;
+    const DiskDev D = disks[d];
+    int64_t lo = 0, hi = D.n0;  // first position whose key is +inf
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (key[D.p_off + mid] < kInfKey) lo = mid + 1; else hi = mid;
+    }
+    n_alive[d] = lo;
+    if (lo == 0 && D.n0 > 0) atomicOr(status, kStEmpty);
+}
+
+__device__ __forceinline__ bool zless(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib)
+{
+    return ka < kb || (ka == kb && ia < ib);
+}
+
+struct ZoneArgs {
+    const mcd_disk_params *params;
+    const DiskDev *disks;
+    const int32_t *zone_disk;
+    const int64_t *n_alive;
+    const uint64_t *rkey;  // sorted r keys
+    const uint32_t *rsrc;  // disk-local source slot of each sorted position
+    const double *m0, *M0, *r0, *z0;
+    const uint32_t *id0;
+    double *m1, *M1, *r1, *z1;
+    uint32_t *id1;
+    int64_t *cell_start;
+    int32_t *cell_n;
+    double *cell_b, *cell_V;
+    int32_t *status;
+};
+
+__global__ void __launch_bounds__(1024) k_zone(ZoneArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int zg = blockIdx.x;
+    const int d = A.zone_disk[zg];
+    const DiskDev D = A.disks[d];
+    const int64_t k = zg - D.z_off;
+    const int64_t Na = A.n_alive[d];
+    const int64_t nr = D.n_r, nz = D.n_z;
+    const int64_t base = Na / nr, rem = Na % nr;
+    const int64_t nk = base + (k < rem ? 1 : 0);
+    const int64_t zs = k * base + (k < rem ? k : rem);
+    const int64_t c0 = D.c_off + k * nz;
+    uint64_t *skey = reinterpret_cast<uint64_t *>(smem_raw);
+    uint32_t *sid = reinterpret_cast<uint32_t *>(skey + nk);
+    uint32_t *ssrc = sid + nk;
+    const uint64_t *rk = A.rkey + D.p_off;
+
+    // (1) load this zone's (z, id, source) triples
+    for (int64_t q = threadIdx.x; q < nk; q += blockDim.x) {
+        uint32_t src = A.rsrc[D.p_off + zs + q];
+        if ((int64_t)src >= D.n0) {  // ids were not a permutation
+            atomicOr(A.status, kStBadCell);
+            src = 0;
+        }
+        int64_t gs = D.p_off + src;
+        double zz = A.z0[gs];
+        if (isnan(zz)) {
+            atomicOr(A.status, kStNaN);
+            zz = INFINITY;
+        }
+        skey[q] = order_key(zz);
+        sid[q] = A.id0[gs];
+        ssrc[q] = src;
+    }
+    __syncthreads();
+    // (2) bitonic sort by (z, id); every compare ascending, i < j, j < nk
+    int64_t P2 = 1;
+    while (P2 < nk) P2 <<= 1;
+    for (int64_t size = 2; size <= P2; size <<= 1) {
+        for (int64_t stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int64_t p = threadIdx.x; p < (P2 >> 1); p += blockDim.x) {
+                int64_t i, j;
+                if (stride == (size >> 1)) {  // first step of a merge: mirror compare
+                    int64_t blk = p / stride, off = p % stride;
+                    i = blk * size + off;
+                    j = blk * size + size - 1 - off;
+                } else {
+                    i = (p / stride) * 2 * stride + p % stride;
+                    j = i + stride;
+                }
+                if (j < nk && zless(skey[j], sid[j], skey[i], sid[i])) {
+                    uint64_t tk = skey[i]; skey[i] = skey[j]; skey[j] = tk;
+                    uint32_t ti = sid[i]; sid[i] = sid[j]; sid[j] = ti;
+                    uint32_t ts = ssrc[i]; ssrc[i] = ssrc[j]; ssrc[j] = ts;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // (3) bounds: radial edges of the zone, then one thread per cell
+    __shared__ double rlo_s, rhi_s;
+    if (threadIdx.x == 0) {
+        double rlo = 0.0, rhi = 0.0;
+        if (nk > 0) {
+            double rf = key_value(rk[zs]), rl = key_value(rk[zs + nk - 1]);
+            int64_t nonempty = Na < nr ? Na : nr;
+            if (Na == 1) {
+                double H = gas_at<double>(A.params[d], rf, 0.0).H;
+                rlo = __dsub_rn(rf, __dmul_rn(0.5, H));
+                rhi = __dadd_rn(rf, __dmul_rn(0.5, H));
+            } else {
+                if (k == 0)
+                    rlo = __dsub_rn(rf, __dmul_rn(__dsub_rn(key_value(rk[1]), rf), 0.5));
+                else
+                    rlo = __dmul_rn(__dadd_rn(key_value(rk[zs - 1]), rf), 0.5);
+                if (k + 1 < nonempty)
+                    rhi = __dmul_rn(__dadd_rn(rl, key_value(rk[zs + nk])), 0.5);
+                else
+                    rhi = __dadd_rn(rl, __dmul_rn(__dsub_rn(rl, key_value(rk[Na - 2])), 0.5));
+            }
+        }
+        rlo_s = rlo;
+        rhi_s = rhi;
+    }
+    __syncthreads();
+    const double rlo = rlo_s, rhi = rhi_s;
+    const double rcen = __dmul_rn(__dadd_rn(rlo, rhi), 0.5);
+    const int64_t zb = nk / nz, zr = nk % nz, nonempty_z = nk < nz ? nk : nz;
+    for (int64_t c = threadIdx.x; c < nz; c += blockDim.x) {
+        int64_t nc = zb + (c < zr ? 1 : 0), cs = c * zb + (c < zr ? c : zr);
+        double zlo = 0.0, zhi = 0.0;
+        if (nc > 0) {
+            double zf = key_value(skey[cs]), zl = key_value(skey[cs + nc - 1]);
+            if (nk == 1) {
+                double H = gas_at<double>(A.params[d], rcen, 0.0).H;
+                zlo = __dsub_rn(zf, __dmul_rn(0.5, H));
+                zhi = __dadd_rn(zf, __dmul_rn(0.5, H));
+            } else {
+                if (c == 0)
+                    zlo = __dsub_rn(zf, __dmul_rn(__dsub_rn(key_value(skey[1]), zf), 0.5));
+                else
+                    zlo = __dmul_rn(__dadd_rn(key_value(skey[cs - 1]), zf), 0.5);
+                if (c + 1 < nonempty_z)
+                    zhi = __dmul_rn(__dadd_rn(zl, key_value(skey[cs + nc])), 0.5);
+                else
+                    zhi = __dadd_rn(zl, __dmul_rn(__dsub_rn(zl, key_value(skey[nk - 2])), 0.5));
+            }
+        }
+        double b0 = nc > 0 ? rlo : 0.0, b1 = nc > 0 ? rhi : 0.0;
+        double *b = A.cell_b + 6 * (c0 + c);
+        b[0] = b0;
+        b[1] = b1;
+        b[2] = zlo;
+        b[3] = zhi;
+        b[4] = __dmul_rn(__dadd_rn(b0, b1), 0.5);
+        b[5] = __dmul_rn(__dadd_rn(zlo, zhi), 0.5);
+        double Ar = __dsub_rn(__dmul_rn(b1, b1), __dmul_rn(b0, b0));
+        A.cell_V[c0 + c] = __dmul_rn(__dmul_rn(kPI, Ar), __dsub_rn(zhi, zlo));
+        A.cell_start[c0 + c] = D.p_off + zs + cs;
+        A.cell_n[c0 + c] = (int32_t)nc;
+    }
+    // (4) gather the particle columns into cell order
+    for (int64_t q = threadIdx.x; q < nk; q += blockDim.x) {
+        int64_t gs = D.p_off + ssrc[q], gd = D.p_off + zs + q;
+        A.m1[gd] = A.m0[gs];
+        A.M1[gd] = A.M0[gs];
+        A.r1[gd] = A.r0[gs];
+        A.z1[gd] = key_value(skey[q]);
+        A.id1[gd] = sid[q];
+    }
+}
+
+// removed particles: sorted positions [n_alive, n0) of each disk, in id order
+__global__ void k_dead_tail(const DiskDev *disks, const int32_t *slot_disk, int64_t N, const int64_t *n_alive,
+                            const uint32_t *rsrc, const double *m0, const double *M0, const double *r0,
+                            const double *z0, const uint32_t *id0, double *m1, double *M1, double *r1, double *z1,
+                            uint32_t *id1)
+{
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    int d = slot_disk[s];
+    const DiskDev D = disks[d];
+    if (s - D.p_off < n_alive[d]) return;
+    int64_t gs = D.p_off + ((int64_t)rsrc[s] < D.n0 ? rsrc[s] : 0);
+    m1[s] = m0[gs];
+    M1[s] = M0[gs];
+    r1[s] = r0[gs];
+    z1[s] = z0[gs];
+    id1[s] = id0[gs];
+}
+
+static size_t zone_smem_bytes(const mcd_ctx *c)
+{
+    int64_t zcap = 0;
+    for (auto &g : c->hg) zcap = zcap > (int64_t)g.n_z * g.per_cell ? zcap : (int64_t)g.n_z * g.per_cell;
+    return (size_t)zcap * 16;
+}
+
+cudaError_t prepare_zone(mcd_ctx *c)
+{
+    return cudaFuncSetAttribute(k_zone, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zone_smem_bytes(c));
+}
+
+cudaError_t launch_regrid(mcd_ctx *c)
+{
+    if (c->N == 0) return cudaSuccess;
+    cudaStream_t st = c->stream;
+    const int b = c->cur, nb = 1 - c->cur;
+    unsigned gN = (unsigned)((c->N + 255) / 256);
+    k_regrid_keys<<<gN, 256, 0, st>>>(c->d_disks, c->slot_disk, c->N, c->r[b], c->z[b], c->id[b], c->key[0],
+                                      c->val[0], c->status);
+    const int64_t H = 256 * c->n_tiles;
+    const unsigned nsb = (unsigned)((H + kScanBlock - 1) / kScanBlock);
+    for (int pass = 0; pass < kRadixPasses; ++pass) {
+        const int shift = 8 * pass, src = pass & 1, dst = src ^ 1;
+        k_radix_hist<<<(unsigned)c->n_tiles, kRadixThreads, 0, st>>>(c->d_disks, c->tile_disk, c->key[src], shift,
+                                                                     c->hist);
+        k_scan_blocks<<<nsb, kScanThreads, 0, st>>>(c->hist, H, c->scan_part);
+        k_scan_parts<<<1, kScanThreads, 0, st>>>(c->scan_part, nsb);
+        k_radix_scatter<<<(unsigned)c->n_tiles, kRadixThreads, 0, st>>>(c->d_disks, c->tile_disk, c->key[src],
+                                                                        c->val[src], c->key[dst], c->val[dst],
+                                                                        shift, c->hist, c->scan_part);
+    }
+    // kRadixPasses is even: the sorted keys are back in buffer 0
+    k_count_alive<<<(c->n_disks + 63) / 64, 64, 0, st>>>(c->d_disks, c->n_disks, c->key[0], c->n_alive, c->status);
+    ZoneArgs A;
+    A.params = c->d_params;
+    A.disks = c->d_disks;
+    A.zone_disk = c->zone_disk;
+    A.n_alive = c->n_alive;
+    A.rkey = c->key[0];
+    A.rsrc = c->val[0];
+    A.m0 = c->m[b]; A.M0 = c->M[b]; A.r0 = c->r[b]; A.z0 = c->z[b]; A.id0 = c->id[b];
+    A.m1 = c->m[nb]; A.M1 = c->M[nb]; A.r1 = c->r[nb]; A.z1 = c->z[nb]; A.id1 = c->id[nb];
+    A.cell_start = c->cell_start;
+    A.cell_n = c->cell_n;
+    A.cell_b = c->cell_b;
+    A.cell_V = c->cell_V;
+    A.status = c->status;
+    size_t sm = zone_smem_bytes(c);
+    k_zone<<<(unsigned)c->Z, 1024, sm, st>>>(A);
+    k_dead_tail<<<gN, 256, 0, st>>>(c->d_disks, c->slot_disk, c->N, c->n_alive, c->val[0], c->m[b], c->M[b], c->r[b],
+                                    c->z[b], c->id[b], c->m[nb], c->M[nb], c->r[nb], c->z[nb], c->id[nb]);
+    c->launches += 4 + 4 * kRadixPasses;
+    return cudaGetLastError();
+}
+
+}  // namespace mcd
