@@ -93,3 +93,26 @@ def random_cell_positions(n: int, seed: int, params: dict) -> tuple[np.ndarray, 
     r = rng.uniform(params["r_in"], params["r_out"], n)
     z = rng.normal(0.0, 1.0, n) * 0.05 * r
     return r, z
+
+
+def midrun_state(params: dict, N: int, seed: int, a_max_1au: float = 10.0, a_slope: float = -1.0,
+                 settle_a: float = 1e-2):
+    """Synthetic particle state shaped like a disk in growth/fragmentation
+    balance, for timing steps away from the all-monomer start.
+
+    Recipe (numpy, seeded): r uniform on [r_in, r_out] (the dust-mass
+    distribution of a p = 1 disk); radii from a mass-weighted n(a) ~ a^-3.5
+    between a_mono and a_max(r) = a_max_1au (r/AU)^a_slope (at least a_mono);
+    z ~ N(0, h) with h = 0.0334 AU (r/AU)^1.25 / sqrt(1 + a/settle_a), a
+    flared scale height that shrinks for large grains.  Returns (m, r, z) for
+    ids 0..N-1; swarm masses and ids come from the initial state."""
+    rng = np.random.Generator(np.random.Philox(key=[seed, 0x5EED]))
+    r = rng.uniform(params["r_in"], params["r_out"], N)
+    a0 = params["a_mono"]
+    amax = np.maximum(a0, a_max_1au * (r / AU) ** a_slope)
+    u = rng.uniform(size=N)
+    a = (np.sqrt(a0) + u * (np.sqrt(amax) - np.sqrt(a0))) ** 2
+    m = 4.0 / 3.0 * np.pi * params["rho_s"] * a**3
+    h = 0.0334 * AU * (r / AU) ** 1.25 / np.sqrt(1.0 + a / settle_a)
+    z = rng.normal(size=N) * h
+    return m, r, z
