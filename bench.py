@@ -100,6 +100,25 @@ def dist_env():
     return rank, world, local
 
 
+def aggregate(total_ms: float, events: int, device=None):
+    """Whole-job numbers over ranks: the slowest rank's time and the summed
+    events.  A timing reduction only; the disks share no data."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return total_ms, events
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    e = torch.tensor([float(events)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return float(t[0]), int(e[0])
+
+
+def rank_seed(base: int, rank: int) -> int:
+    """Each rank simulates its own disk: same physics, its own random stream."""
+    return base + rank
+
+
 def workload(args):
     from paper_2507_21239_gb300 import workloads as W
     wl = W.WORKLOADS[args.workload]
@@ -111,7 +130,7 @@ def make_state(args, ctx_or_none, rank):
     """Synthetic mid-run state: m, r, z from the recipe; M, id from the initial state."""
     W, wl, P, grid = workload(args)
     N = grid[0] * grid[1] * grid[2]
-    m, r, z = W.midrun_state(P, N, seed=wl["seed"] + rank)
+    m, r, z = W.midrun_state(P, N, seed=rank_seed(wl["seed"], rank))
     return P, grid, N, m, r, z
 
 
@@ -201,10 +220,10 @@ def run_ours(args):
     B.build()
     W, wl, P, grid = workload(args)
     N = grid[0] * grid[1] * grid[2]
-    seed = wl["seed"] + rank
+    seed = rank_seed(wl["seed"], rank)
     dt = args.dt_yr * W.YR
     stream = torch.cuda.Stream(device=dev)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    flush = torch.empty(max(args.flush_mb, 1) << 20, dtype=torch.uint8, device=dev)
     _, _, _, m, r, z = make_state(args, None, rank)
 
     def fresh(prec):
@@ -238,12 +257,7 @@ def run_ours(args):
     status = mcd.mcd_sync(d.ctx)
     events = st1.events - st0.events
     total_ms = float(times.sum())
-    if world > 1:
-        t = torch.tensor([total_ms, float(events)], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
-        total_ms, events = float(tmax[0]), int(t[1])
+    total_ms, events = aggregate(total_ms, events, device=dev)
     value = events / (total_ms * 1e-3)
     yr_per_s = args.steps * args.dt_yr / (total_ms * 1e-3)
     # cell populations for the algorithmic flop count of the collide kernel
@@ -274,7 +288,7 @@ def run_ours(args):
            "config": {"workload": args.workload, "particles_per_gpu": N, "cells_per_gpu": grid[0] * grid[1],
                       "dt_yr": args.dt_yr, "precision": "mixed",
                       "state": "synthetic growth/fragmentation-balance state (workloads.midrun_state)",
-                      "l2": "512 MB buffer written between timed steps; each step timed alone",
+                      "l2": f"{args.flush_mb} MB buffer written between timed steps; each step timed alone",
                       "graph": "step replayed as one CUDA graph", "parallelism": f"{world} independent disks"},
            "phases_ms": {"regrid": ph[0], "order": ph[1], "collide": ph[2], "transport": ph[3]},
            "roofline": dom, "roofline_all": {"collide": coll, "regrid": reg, "transport": tra},
@@ -353,6 +367,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
+    ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -101,6 +101,7 @@ size_t carve(mcd_ctx *c, void *base, const Sizes &S, int32_t nd)
     x->cell_n = cv.take<int32_t>(S.C);
     x->cell_b = cv.take<double>(6 * S.C);
     x->cell_V = cv.take<double>(S.C);
+    x->cellk = cv.take<unsigned char>((size_t)S.C * kCellKBytes);
     x->cell_events = cv.take<int64_t>(S.C);
     x->cell_cost = cv.take<uint32_t>(S.C);
     x->queue = cv.take<int32_t>(S.C);

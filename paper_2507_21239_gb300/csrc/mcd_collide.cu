@@ -8,18 +8,26 @@
 //
 // GB300 layout: one CTA per cell, one thread per swarm (n <= kMaxCell).  The
 // per-swarm cache (radius, Stokes number, drag-law flags, 1/m, M/V, ...) sits
-// in shared memory; each thread keeps its own row sum R_k in registers.  One
-// event costs two block scans (choose i, choose j), two row evaluations (n
-// kernel entries each, one per thread) and one block reduction.
+// in shared memory; each thread keeps its own row sum R_k in registers.  The
+// per-cell gas constants come from a separate one-thread-per-cell kernel.
+// One event = a block scan that chooses i (and folds in the previous event's
+// fresh R_i), one kernel entry per thread for row/column i, a block scan
+// that chooses j, the outcome on one thread, and one more kernel entry per
+// thread for the new row/column i: five block barriers.
 //
 // Precision (template T): T = double is the plain FP64 path.  T = float is
-// the mixed path: dv, sigma, K and the rates in FP32; masses, the cell clock
-// and sticking additions in FP64; row sums R_k as compensated FP32 pairs.
-// Differences of Stokes numbers use a factored difference of cubes over
-// masses split into (hi, lo) FP32 pairs, so close masses lose no digits, and
-// drag-law and turbulence regimes are decided by FP64 mass thresholds.
+// the mixed path: dv, sigma, K, rates, waiting times and partner choice in
+// FP32; masses and the cell clock in FP64 (kept by one thread, off the
+// critical path, because an FP64 instruction costs ~64 cycles on GB300);
+// row sums R_k as compensated FP32 pairs.  Stokes-number differences use a
+// factored difference of cubes over masses split into (hi, lo) FP32 pairs and
+// St itself is carried as a (hi, lo) pair, so close masses lose no digits;
+// drag-law and turbulence regimes are decided by mass thresholds held as
+// (hi, lo) pairs of the FP64 values.
 #include <float.h>
 #include <math.h>
+
+#include <type_traits>
 
 #include "mcd_internal.cuh"
 
@@ -31,7 +39,7 @@ struct alignas(16) Part {
     T a, S, p, q;      // radius, Stokes number, 1/(1+S^2), 1/(1+S)
     T im, mh, ml, ad;  // 1/m, mass as hi+lo, (a - a_sw) for Stokes-law swarms
     T Mv, gi;          // M/V (times the cell's rate scale), 1/(dm m) (inf: no grouping)
-    T Sl;              // low part of S (FP32 path: S = S + Sl to ~2^-44)
+    T Sl;              // low part of S (FP32 path: S + Sl to ~2^-44)
     int32_t fl;        // turbulence regime (0,1,2) | stokes << 2
 };
 
@@ -39,10 +47,20 @@ struct alignas(16) Part {
 template <class T>
 struct CellK {
     T Cep, Cst, cm, asw, vg2, Se, cbm, e4, e1, oz2, Kc, pi;
+    T Cep_lo, Cst_lo, cm_lo;                         // low parts (FP32 path)
+    T msw_h, msw_l, meta_h, meta_l, mone_h, mone_l;  // mass thresholds as hi + lo
+    T invVsc_t, dm_t, vfrag_t;
     int32_t kmode, settle;
     double m_sw, m_eta, m_one, m0, V, sc, invVsc, vfrag, ratio, chi, dm, fe, cm_d;
-    T Cep_lo, Cst_lo;  // FP32 path: low parts of the drag constants
 };
+static_assert(sizeof(CellK<double>) <= kCellKBytes && sizeof(CellK<float>) <= kCellKBytes, "cell constants");
+
+template <class T>
+__device__ __forceinline__ void split(double x, T &h, T &l)
+{
+    h = (T)x;
+    l = (T)(x - (double)h);
+}
 
 template <class T>
 __device__ CellK<T> make_cell(const mcd_disk_params &P, double rc, double zc, double V, double Mref)
@@ -62,9 +80,12 @@ __device__ CellK<T> make_cell(const mcd_disk_params &P, double rc, double zc, do
     c.m_eta = m_at(g.St_eta);
     c.m_one = m_at(1.0);
     int f = P.dv_flags;
-    c.Cep = (T)Cep;
-    c.Cst = (T)Cst;
-    c.cm = (T)cm;
+    split(Cep, c.Cep, c.Cep_lo);
+    split(Cst, c.Cst, c.Cst_lo);
+    split(cm, c.cm, c.cm_lo);
+    split(c.m_sw, c.msw_h, c.msw_l);
+    split(c.m_eta, c.meta_h, c.meta_l);
+    split(c.m_one, c.mone_h, c.mone_l);
     c.cm_d = cm;
     c.asw = (T)g.asw;
     c.vg2 = (f & MCD_DV_TURB) ? (T)g.vg2 : (T)0;
@@ -79,29 +100,30 @@ __device__ CellK<T> make_cell(const mcd_disk_params &P, double rc, double zc, do
     c.kmode = P.kernel_mode;
     c.settle = P.settle_form;
     c.V = P.kernel_mode == 1 ? P.V_const : V;
-    if (sizeof(T) == 4 && Mref > 0.0 && c.V > 0.0) {
-        // power-of-two rate scale keeping M/V near 1 in FP32
-        c.sc = ldexp(1.0, -ilogb(Mref / c.V));
-    } else {
-        c.sc = 1.0;
-    }
+    // FP32 path: a power-of-two rate scale keeping M/V near 1
+    c.sc = (sizeof(T) == 4 && Mref > 0.0 && c.V > 0.0) ? ldexp(1.0, -ilogb(Mref / c.V)) : 1.0;
     c.invVsc = c.V > 0.0 ? c.sc / c.V : 0.0;
+    c.invVsc_t = (T)c.invVsc;
     c.m0 = monomer_mass(P);
     c.vfrag = P.v_frag;
+    c.vfrag_t = (T)P.v_frag;
     c.ratio = P.erosion_ratio;
     c.chi = P.erosion_chi;
     c.dm = P.dm_group;
+    c.dm_t = (T)P.dm_group;
     c.fe = 2.0 - P.frag_xi;
-    c.Cep_lo = (T)(Cep - (double)c.Cep);
-    c.Cst_lo = (T)(Cst - (double)c.Cst);
     return c;
 }
 
+// (ah, al) < (bh, bl) for normalised hi + lo pairs
+__device__ __forceinline__ bool pair_lt(float ah, float al, float bh, float bl) { return ah < bh || (ah == bh && al < bl); }
+
+// Per-swarm cache from the mass and the swarm's M/V (times the rate scale).
 template <class T>
-__device__ __forceinline__ Part<T> make_part(const CellK<T> &c, double m, double M);
+__device__ __forceinline__ Part<T> make_part(const CellK<T> &c, double m, T Mv);
 
 template <>
-__device__ __forceinline__ Part<double> make_part<double>(const CellK<double> &c, double m, double M)
+__device__ __forceinline__ Part<double> make_part<double>(const CellK<double> &c, double m, double Mv)
 {
     Part<double> q;
     bool stk = m >= c.m_sw;
@@ -110,34 +132,36 @@ __device__ __forceinline__ Part<double> make_part<double>(const CellK<double> &c
     q.ml = 0.0;
     q.a = cbrt(c.cm_d * m);
     q.S = stk ? c.Cst * q.a * q.a : c.Cep * q.a;
+    q.Sl = 0.0;
     q.p = 1.0 / (1.0 + q.S * q.S);
     q.q = 1.0 / (1.0 + q.S);
     q.im = 1.0 / m;
     q.ad = stk ? c.cm_d * (m - c.m_sw) / ((q.a * q.a + c.asw * c.asw) + q.a * c.asw) : 0.0;
-    q.Mv = M * c.invVsc;
+    q.Mv = Mv;
     q.gi = c.dm > 0.0 ? 1.0 / (c.dm * m) : (double)INFINITY;
     q.fl = cls | ((int)stk << 2);
-    q.Sl = 0.0;
     return q;
 }
 
+// FP32 path: one FP64 instruction (the lo part of the mass), the rest FP32.
 template <>
-__device__ __forceinline__ Part<float> make_part<float>(const CellK<float> &c, double m, double M)
+__device__ __forceinline__ Part<float> make_part<float>(const CellK<float> &c, double m, float Mv)
 {
     Part<float> q;
-    bool stk = m >= c.m_sw;
-    int cls = m < c.m_eta ? 0 : (m < c.m_one ? 1 : 2);
-    q.mh = (float)m;
-    q.ml = (float)(m - (double)q.mh);
-    // a = cbrt(cm m) to about 2^-44: FP32 cube root plus one Newton step on the
-    // residual x - a0^3 taken exactly with fused multiply-adds
-    double xd = c.cm_d * m;
-    float xh = (float)xd, xl = (float)(xd - (double)xh);
-    float a0 = cbrtf(xh);
-    float p2 = a0 * a0, p2e = fmaf(a0, a0, -p2);   // a0^2 = p2 + p2e
-    float p3 = p2 * a0, p3e = fmaf(p2, a0, -p3);   // p2 a0 = p3 + p3e
-    float res = (((xh - p3) - p3e) - p2e * a0) + xl; // x - a0^3
-    float alo = res / (3.0f * p2);
+    float mh = (float)m, ml = (float)(m - (double)mh);
+    q.mh = mh;
+    q.ml = ml;
+    bool stk = !pair_lt(mh, ml, c.msw_h, c.msw_l);
+    int cls = pair_lt(mh, ml, c.meta_h, c.meta_l) ? 0 : (pair_lt(mh, ml, c.mone_h, c.mone_l) ? 1 : 2);
+    // x = cm m as a (hi, lo) pair, then a = cbrt(x) to about 2^-44: FP32 cube
+    // root plus one Newton step on the residual x - a0^3 taken exactly
+    float xh = c.cm * mh;
+    float xl = fmaf(c.cm, mh, -xh) + c.cm * ml + c.cm_lo * mh;
+    float a0 = exp2f(__log2f(xh) * (1.0f / 3.0f));  // refined to full precision below
+    float p2 = a0 * a0, p2e = fmaf(a0, a0, -p2);     // a0^2 = p2 + p2e
+    float p3 = p2 * a0, p3e = fmaf(p2, a0, -p3);     // p2 a0 = p3 + p3e
+    float res = (((xh - p3) - p3e) - p2e * a0) + xl;  // x - a0^3
+    float alo = res * __fdividef(1.0f, 3.0f * p2);
     q.a = a0;
     float Sh, Se;
     if (stk) {  // S = Cst a^2 = Cst (p2 + p2e + 2 a0 alo)
@@ -149,24 +173,47 @@ __device__ __forceinline__ Part<float> make_part<float>(const CellK<float> &c, d
     }
     q.S = Sh + Se;
     q.Sl = Se - (q.S - Sh);
-    q.p = 1.0f / (1.0f + q.S * q.S);
-    q.q = 1.0f / (1.0f + q.S);
-    q.im = 1.0f / q.mh;
-    q.ad = stk ? (float)(c.cm_d * (m - c.m_sw)) / ((q.a * q.a + c.asw * c.asw) + q.a * c.asw) : 0.0f;
-    q.Mv = (float)(M * c.invVsc);
-    q.gi = c.dm > 0.0 ? 1.0f / ((float)c.dm * q.mh) : INFINITY;
+    q.p = __fdividef(1.0f, 1.0f + q.S * q.S);
+    q.q = __fdividef(1.0f, 1.0f + q.S);
+    q.im = __fdividef(1.0f, mh);
+    // a - a_sw = cm (m - m_sw) / (a^2 + a a_sw + a_sw^2), m - m_sw from the pairs
+    float dsw = (mh - c.msw_h) + (ml - c.msw_l);
+    q.ad = stk ? c.cm * dsw * __fdividef(1.0f, (a0 * a0 + c.asw * c.asw) + a0 * c.asw) : 0.0f;
+    q.Mv = Mv;
+    q.gi = c.dm_t > 0.0f ? __fdividef(1.0f, c.dm_t * mh) : INFINITY;
     q.fl = cls | ((int)stk << 2);
     return q;
 }
 
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+
+// The constants one kernel entry reads; the FP32 path keeps them in registers
+// (read from shared memory at every entry they would sit on the critical path).
+template <class T>
+struct PairK {
+    T Cep, Cst, cm, asw, vg2, Se, cbm, e4, e1, oz2, Kc, pi;
+    int32_t kmode, settle;
+};
+
+template <class T>
+__device__ __forceinline__ PairK<T> pair_consts(const CellK<T> &c)
+{
+    PairK<T> p;
+    p.Cep = c.Cep, p.Cst = c.Cst, p.cm = c.cm, p.asw = c.asw, p.vg2 = c.vg2, p.Se = c.Se;
+    p.cbm = c.cbm, p.e4 = c.e4, p.e1 = c.e1, p.oz2 = c.oz2, p.Kc = c.Kc, p.pi = c.pi;
+    p.kmode = c.kmode, p.settle = c.settle;
+    return p;
+}
 
 // Relative velocity of a pair (symmetric in its arguments bit for bit):
 // Brownian motion, Ormel & Cuzzi (2007) turbulence, radial and azimuthal
-// drift and settling, summed in quadrature.  Returns dv; K via *K.
-template <class T>
-__device__ __forceinline__ T pair_dv(const CellK<T> &c, const Part<T> &u, const Part<T> &v, T *K)
+// drift and settling, summed in quadrature.  Returns dv; K via *K.  C is
+// CellK<T> or PairK<T>.
+template <class T, class C>
+__device__ __forceinline__ T pair_dv(const C &c, const Part<T> &u, const Part<T> &v, T *K)
 {
     if (c.kmode == 1) {
         *K = c.Kc;
@@ -175,29 +222,57 @@ __device__ __forceinline__ T pair_dv(const CellK<T> &c, const Part<T> &u, const 
     // |St_u - St_v| from the factored difference of cubes
     T dm = fabs((u.mh - v.mh) + (u.ml - v.ml));
     T den = fma(u.a, v.a, mul_rn(u.a, u.a) + mul_rn(v.a, v.a));
-    T da = c.cm * dm / den;
+    T da = fdiv(c.cm * dm, den);
     int su = u.fl >> 2, sv = v.fl >> 2;
-    T D;
-    if (su & sv) {
-        D = c.Cst * (u.a + v.a) * da;
-    } else if (su | sv) {
-        T as = su ? u.a : v.a, ads = su ? u.ad : v.ad;
-        D = c.Cst * fma(as, ads, c.asw * da);
-    } else {
-        D = c.Cep * da;
-    }
     T S1 = fmax(u.S, v.S), S2 = fmin(u.S, v.S);
     int cls = max(u.fl & 3, v.fl & 3);
-    T tv;
-    if (cls == 0) {
+    T D, tv;
+    if (sizeof(T) == 4) {
+        // FP32: every case evaluated and selected, so the lanes of a warp
+        // never diverge (the regimes mix freely within a cell).  dv^2 is
+        // factored as t0 + D^2 coef: everything but D (including the regime-I
+        // division) is computed alongside D's own division.
+        T as = su ? u.a : v.a, ads = su ? u.ad : v.ad;
+        T D_st = c.Cst * (u.a + v.a) * da, D_mx = c.Cst * fma(as, ads, c.asw * da), D_ep = c.Cep * da;
+        D = (su & sv) ? D_st : ((su | sv) ? D_mx : D_ep);
         T s = S1 + S2;
-        tv = s > (T)0 ? c.vg2 * D * D * fma(S1, S2, c.Se * s) / (s * (S1 + c.Se) * (S2 + c.Se)) : (T)0;
-    } else if (cls == 1) {
-        T eps = S2 / S1, ope = (T)1 + eps;
-        tv = c.vg2 * S1 *
-             (((T)(2.0 * kYA) - ope) + (T)2 / ope * ((T)(1.0 / (1.0 + kYA)) + eps * eps * eps / ((T)kYA + eps)));
+        T g1 = fdiv(c.vg2 * fma(S1, S2, c.Se * s), s * (S1 + c.Se) * (S2 + c.Se));  // regime I: D^2 g1
+        T eps = fdiv(S2, S1), ope = (T)1 + eps, yae = (T)kYA + eps;
+        T last = fdiv((T)2 * (yae * (T)(1.0 / (1.0 + kYA)) + eps * eps * eps), ope * yae);
+        T t2 = c.vg2 * S1 * (((T)(2.0 * kYA) - ope) + last);
+        T t3 = c.vg2 * (u.q + v.q);
+        T pp = u.p * v.p;
+        T om = fma(-u.S, v.S, (T)1) - (mul_rn(u.S, v.Sl) + mul_rn(u.Sl, v.S));
+        T sp = S1 + S2;
+        T qq = c.settle ? (u.q * v.q) * (u.q * v.q) : (T)1;
+        T coef = pp * pp * (c.e4 * om * om + c.e1 * sp * sp) + c.oz2 * qq + ((cls == 0 && s > (T)0) ? g1 : (T)0);
+        T t0 = c.cbm * (u.im + v.im) + (cls == 1 ? t2 : (cls == 2 ? t3 : (T)0));
+        T dv2 = fma(D * D, coef, t0);
+        T dv = dv2 > (T)0 ? dv2 * rsqrtf(dv2) : (T)0;
+        T s2 = u.a + v.a;
+        *K = c.pi * s2 * s2 * dv;
+        return dv;
     } else {
-        tv = c.vg2 * (u.q + v.q);
+        if (su & sv) {
+            D = c.Cst * (u.a + v.a) * da;
+        } else if (su | sv) {
+            T as = su ? u.a : v.a, ads = su ? u.ad : v.ad;
+            D = c.Cst * fma(as, ads, c.asw * da);
+        } else {
+            D = c.Cep * da;
+        }
+        if (cls == 0) {
+            T s = S1 + S2;
+            tv = s > (T)0 ? fdiv(c.vg2 * D * D * fma(S1, S2, c.Se * s), s * (S1 + c.Se) * (S2 + c.Se)) : (T)0;
+        } else if (cls == 1) {
+            // vg2 S1 [2 y_a - (1+e) + 2/(1+e) (1/(1+y_a) + e^3/(y_a+e))], the last
+            // term over one common denominator
+            T eps = fdiv(S2, S1), ope = (T)1 + eps, yae = (T)kYA + eps;
+            T last = fdiv((T)2 * (yae * (T)(1.0 / (1.0 + kYA)) + eps * eps * eps), ope * yae);
+            tv = c.vg2 * S1 * (((T)(2.0 * kYA) - ope) + last);
+        } else {
+            tv = c.vg2 * (u.q + v.q);
+        }
     }
     T pp = u.p * v.p;
     // 1 - S_u S_v with the product taken exactly and the low parts added
@@ -223,34 +298,63 @@ __device__ __forceinline__ T weight(const Part<T> &self, const Part<T> &other)
     return other.Mv * fmin(other.im, self.gi);
 }
 
-// ---- block scan --------------------------------------------------------------
-template <class V>
-__device__ __forceinline__ void block_scan(V x, V *buf, V &incl, V &excl, V &total)
+// ---- partner choice ----------------------------------------------------------
+// Choose k with probability x_k / total: the first k whose inclusive prefix
+// exceeds u * total.  With FUSE the scan also sums y over the block (the
+// previous event's new row) and folds that sum in as element pend's value
+// (x_pend is then 0).  A shuffle scan within each warp, then a shuffle scan of
+// the warp totals held one per lane; every warp knows the range [lo, hi) of
+// the prefix it covers, lo of warp w+1 bit-identical to hi of warp w, so
+// exactly one warp brackets the target and finds the element by a ballot.
+// Two barriers; the result is broadcast through shared memory.
+template <class V, bool FUSE>
+__device__ __forceinline__ int block_choose(V x, V y, V u, int pend, V *buf, int *sel, V &total, V &ysum)
 {
     const unsigned FULL = 0xffffffffu;
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    V wi = x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    V wi = x, ys = y;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        V y = __shfl_up_sync(FULL, wi, o);
-        if (lane >= o) wi += y;
+        V a = __shfl_up_sync(FULL, wi, o);
+        if (lane >= o) wi += a;
+        if (FUSE) ys += __shfl_xor_sync(FULL, ys, o);
     }
-    V we = __shfl_up_sync(FULL, wi, 1);
-    if (lane == 0) we = (V)0;
-    if (lane == 31) buf[w] = wi;
+    if (lane == 31) {
+        buf[2 * w] = wi;
+        buf[2 * w + 1] = ys;
+    }
     __syncthreads();
-    V off = (V)0, tot = (V)0;
-    for (int k = 0; k < nw; ++k) {
-        V b = buf[k];
-        if (k < w) off += b;
-        tot += b;
+    // lane q holds warp q's total (q < nw <= 16); scan them in registers
+    V bt = lane < nw ? buf[2 * lane] : (V)0;
+    V by = (FUSE && lane < nw) ? buf[2 * lane + 1] : (V)0;
+    V bs = bt;
+#pragma unroll
+    for (int o = 1; o < kMaxCell / 32; o <<= 1) {
+        V a = __shfl_up_sync(FULL, bs, o);
+        if (lane >= o) bs += a;
+        if (FUSE) by += __shfl_xor_sync(FULL, by, o);
     }
-    incl = off + wi;
-    excl = off + we;
-    total = tot;
+    const V tot = __shfl_sync(FULL, bs, nw - 1);
+    const V prev = __shfl_sync(FULL, bs, w > 0 ? w - 1 : 0);
+    const V off = w > 0 ? prev : (V)0;
+    const V hib = __shfl_sync(FULL, bs, w);
+    const V Rp = (FUSE && pend >= 0) ? __shfl_sync(FULL, by, 0) : (V)0;
+    total = tot + Rp;
+    ysum = Rp;
+    V target = u * total;
+    if (target >= total) target = total * (V)(1.0 - 1e-7);
+    const int k = threadIdx.x;
+    const V P = (off + wi) + ((pend >= 0 && k >= pend) ? Rp : (V)0);
+    const V lo = off + ((pend >= 0 && 32 * w > pend) ? Rp : (V)0);
+    const V hi = hib + ((pend >= 0 && 32 * w + 31 >= pend) ? Rp : (V)0);
+    const unsigned bal = __ballot_sync(FULL, P > target);
+    // (a tree scan may leave lane 31's prefix an ulp below hi: then lane 31)
+    if (lane == 0 && lo <= target && target < hi) *sel = 32 * w + __ffs(bal | 0x80000000u) - 1;
+    __syncthreads();
+    return *sel;
 }
 
-// ---- fragments -----------------------------------------------------------------
+// ---- outcomes ----------------------------------------------------------------
 // mass-weighted draw on [m0, mmax] from n(m) ~ m^-xi, e = 2 - xi:
 // m = m0 [1 + u ((mmax/m0)^e - 1)]^(1/e), in expm1/log1p form (relative
 // precision kept when mmax is close to m0)
@@ -259,7 +363,7 @@ __device__ double frag_draw(double m0, double fe, double mmax, double u, bool fp
     if (mmax <= m0) return m0;
     double m;
     if (fp32) {
-        float L = logf((float)(mmax / m0)), e = (float)fe;
+        float L = logf(__fdividef((float)mmax, (float)m0)), e = (float)fe;
         m = fabs(fe) < 1e-12 ? m0 * (double)expf((float)u * L)
                              : m0 * (double)expf(log1pf((float)u * expm1f(e * L)) / e);
     } else {
@@ -269,18 +373,23 @@ __device__ double frag_draw(double m0, double fe, double mmax, double u, bool fp
     return fmin(fmax(m, m0), mmax);
 }
 
+// order of positive finite doubles through their bit patterns (integer unit)
+__device__ __forceinline__ bool dgt(double a, double b) { return __double_as_longlong(a) > __double_as_longlong(b); }
+
+// new mass of representative i after meeting a particle of swarm j; dmmi is
+// dm m_i (0 when grouping is off), computed ahead by the caller
 template <class T>
-__device__ double outcome(const CellK<T> &c, double mi, double mj, double dv, double u3, int &kind)
+__device__ double outcome(const CellK<T> &c, double mi, double mj, double dmmi, T dv, double u3, int &kind)
 {
-    double gain = (c.dm > 0.0 && c.dm * mi > mj) ? c.dm * mi : mj;
-    if (c.kmode == 1 || dv < c.vfrag) {
+    double gain = dgt(dmmi, mj) ? dmmi : mj;  // N_g m_j
+    if (c.kmode == 1 || dv < (sizeof(T) == 4 ? (T)c.vfrag_t : (T)c.vfrag)) {
         kind = 0;
         return mi + gain;
     }
-    double big = fmax(mi, mj), small = fmin(mi, mj);
+    double big = dgt(mi, mj) ? mi : mj, small = dgt(mi, mj) ? mj : mi;
     if (big >= c.ratio * small) {
         kind = 2;
-        if (mi >= mj) {
+        if (!dgt(mj, mi)) {
             double mn = mi - c.chi * gain;
             return mn > c.m0 ? mn : c.m0;
         }
@@ -298,6 +407,7 @@ struct Acc<double> {
     double s;
     __device__ void zero() { s = 0.0; }
     __device__ void add(double x) { s += x; }
+    __device__ void update(double n, double o) { s += n - o; }
     __device__ double hi() const { return s; }
     __device__ double value() const { return s; }
     __device__ void set(double x) { s = x; }
@@ -313,10 +423,41 @@ struct Acc<float> {
         c += (s - (t - bp)) + (x - bp);
         s = t;
     }
+    __device__ void update(float n, float o)
+    {
+        add(n);
+        add(-o);
+    }
     __device__ float hi() const { return s + c; }
     __device__ double value() const { return (double)s + (double)c; }
     __device__ void set(float x) { s = x, c = 0.0f; }
 };
+
+// random numbers of one event: -log(u0) (times the rate scale), u1, u2, u3
+template <class T>
+struct Draw {
+    T L, u1, u2, u3;
+};
+
+__device__ __forceinline__ Draw<float> make_draw(const U4 &x, float sc)
+{
+    Draw<float> d;
+    d.L = -logf(u01f(x.x[0])) * sc;
+    d.u1 = u01f(x.x[1]);
+    d.u2 = u01f(x.x[2]);
+    d.u3 = u01f(x.x[3]);
+    return d;
+}
+
+__device__ __forceinline__ Draw<double> make_draw(const U4 &x, double sc)
+{
+    Draw<double> d;
+    d.L = -log(u01d(x.x[0])) * sc;
+    d.u1 = u01d(x.x[1]);
+    d.u2 = u01d(x.x[2]);
+    d.u3 = u01d(x.x[3]);
+    return d;
+}
 
 struct CollideArgs {
     const mcd_disk_params *params;
@@ -325,7 +466,8 @@ struct CollideArgs {
     const int64_t *cell_start;
     const int32_t *cell_n;
     const double *cell_b, *cell_V;
-    const int32_t *queue;  // block -> cell (null: identity)
+    const unsigned char *cellk;  // per-cell constants, kCellKBytes each
+    const int32_t *queue;        // block -> cell (null: identity)
     double *m;
     const double *M;
     int64_t *cell_events;
@@ -349,12 +491,26 @@ struct CollideArgs {
 template <class T>
 struct Shared {
     CellK<T> c;
-    T scan[4][32];
-    int sel[4];
-    double ring[32][4];  // -log u0, u1, u2, u3
-    double mnew;
-    int i_ev, j_ev;
+    T scan[2][64];
+    int sel[2];
+    Draw<T> ring[32];
+    double tnew;
+    int stop;
 };
+
+// per-cell constants: one thread per cell, all SMs (the FP64 gas evaluation is
+// long; done here it leaves the collide CTAs' critical path)
+template <class T>
+__global__ void k_cellconst(const mcd_disk_params *params, const int32_t *cell_disk, const int64_t *cell_start,
+                            const int32_t *cell_n, const double *cell_b, const double *cell_V, const double *M,
+                            unsigned char *cellk, int64_t C)
+{
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= C || cell_n[c] <= 0) return;
+    const double *b = cell_b + 6 * c;
+    *reinterpret_cast<CellK<T> *>(cellk + c * kCellKBytes) =
+        make_cell<T>(params[cell_disk[c]], b[4], b[5], cell_V[c], M[cell_start[c]]);
+}
 
 template <class T>
 __global__ void __launch_bounds__(kMaxCell) k_collide(CollideArgs A)
@@ -379,145 +535,152 @@ __global__ void __launch_bounds__(kMaxCell) k_collide(CollideArgs A)
         return;
     }
     const int disk = A.cell_disk[cell];
-    const mcd_disk_params &P = A.params[disk];
     const int64_t off = A.cell_start[cell];
-    const double t0 = A.state->t;
-    const double t_end = A.t_end_from_state ? t0 + A.state->dt : A.t_end_fixed;
-    const uint64_t step = (uint64_t)A.state->step;
-
-    if (k == 0) {
-        const double *b = A.cell_b + 6 * cell;
-        sh.c = make_cell<T>(P, b[4], b[5], A.cell_V[cell], A.M[off]);
-    }
+    if (k == 0) sh.c = *reinterpret_cast<const CellK<T> *>(A.cellk + cell * kCellKBytes);
     __syncthreads();
     const CellK<T> &c = sh.c;
+    // FP32: the entry constants in registers; FP64: read in place (register budget)
+    typedef typename std::conditional<sizeof(T) == 4, PairK<T>, const CellK<T> &>::type PK;
+    PK pc = [&]() -> PK {
+        if constexpr (sizeof(T) == 4) return pair_consts<T>(sh.c); else return sh.c;
+    }();
     const bool active = k < n;
     Part<T> pk;
     if (active) {
         double mk = A.m[off + k];
         msh[k] = mk;
-        pk = make_part<T>(c, mk, A.M[off + k]);
+        pk = make_part<T>(c, mk, (T)(A.M[off + k] * c.invVsc));
         parts[k] = pk;
     }
     __syncthreads();
 
-
     Acc<T> R;
+    // R_k = sum_j r_kj in j order; four independent kernel entries in flight
     auto rebuild = [&]() {
         R.zero();
         if (active) {
-            for (int j = 0; j < n; ++j) {
-                Part<T> pj = parts[j];
+            int j = 0;
+            // (FP64: no unrolling; its register budget is spent on the wider values)
+            for (; sizeof(T) == 4 && j + 4 <= n; j += 4) {
+                T K0, K1, K2, K3;
+                const Part<T> p0 = parts[j], p1 = parts[j + 1], p2 = parts[j + 2], p3 = parts[j + 3];
+                pair_dv<T>(pc, pk, p0, &K0);
+                pair_dv<T>(pc, pk, p1, &K1);
+                pair_dv<T>(pc, pk, p2, &K2);
+                pair_dv<T>(pc, pk, p3, &K3);
+                R.add(K0 * weight<T>(pk, p0));
+                R.add(K1 * weight<T>(pk, p1));
+                R.add(K2 * weight<T>(pk, p2));
+                R.add(K3 * weight<T>(pk, p3));
+            }
+            for (; j < n; ++j) {
+                const Part<T> pj = parts[j];
                 T K;
-                pair_dv<T>(c, pk, pj, &K);
+                pair_dv<T>(pc, pk, pj, &K);
                 R.add(K * weight<T>(pk, pj));
             }
         }
     };
     rebuild();
 
-    const int64_t reb = A.rebuild_every > 0 ? A.rebuild_every : (int64_t)n;
     // the random stream is keyed by (seed, disk) and counted by
     // (event, disk-local cell, step, domain tag)
     const uint64_t dcell = (uint64_t)(cell - A.disks[disk].c_off);
-    double t = t0;
-    int64_t ev = 0;
-    int sb = 0;  // scan buffer rotation
+    const uint64_t step = (uint64_t)A.state->step;
+    const double t_end = A.t_end_from_state ? A.state->t + A.state->dt : A.t_end_fixed;
+    const int64_t reb = A.rebuild_every > 0 ? A.rebuild_every : (int64_t)n;
+    int64_t until_rebuild = reb;  // events left before the next full rebuild
     const bool logging = (cell == A.log_cell);
-    const double sc = c.sc;
+    const T sc = (T)c.sc;
+    double t = A.state->t;  // the cell clock, kept by the block's last thread
+    const int kclk = blockDim.x - 1;
+    int64_t ev = 0;
+    int pend = -1;          // swarm whose fresh row sum rides on the next scan
+    T rown = (T)0;          // this thread's entry of that row
     for (;;) {
         if ((ev & 31) == 0) {
-            if (k < 32) {
-                U4 x = philox((uint64_t)(ev + k), dcell, step, kTagCollide, A.seed, (uint64_t)disk);
-                sh.ring[k][0] = -log(u01d(x.x[0]));
-                sh.ring[k][1] = u01d(x.x[1]);
-                sh.ring[k][2] = u01d(x.x[2]);
-                sh.ring[k][3] = u01d(x.x[3]);
-            }
+            if (k < 32)
+                sh.ring[k] = make_draw(philox((uint64_t)(ev + k), dcell, step, kTagCollide, A.seed, (uint64_t)disk), sc);
             __syncthreads();
         }
-        const int slot = (int)(ev & 31);
-        // choose i: first k whose inclusive prefix of R exceeds u1 R_tot
-        T val = active ? (T)R.hi() : (T)0;
-        T incl, excl, tot;
-        if (k == 0) sh.sel[(sb + 1) & 3] = -1;  // ordered before any hit by the scan's barrier
-        block_scan<T>(val, sh.scan[sb], incl, excl, tot);
-        sb = (sb + 1) & 3;
+        const Draw<T> dr = sh.ring[ev & 31];
+        // (1) choose i: first k whose inclusive prefix of R exceeds u1 R_tot;
+        //     the previous event's R_i (sum of its new row) is folded in here
+        T val = (active && k != pend) ? (T)R.hi() : (T)0;
+        T tot, Rp;
+        if (k == 0) sh.sel[0] = -1;
+        int i = block_choose<T, true>(val, rown, dr.u1, pend, sh.scan[0], &sh.sel[0], tot, Rp);
+        if (pend >= 0 && k == pend) R.set(Rp);
         if (!(tot > (T)0)) break;
         if (ev >= A.max_events) {
             if (!A.cap_stops && k == 0) atomicOr(A.status, kStTimeout);
             break;
         }
-        double tau = sh.ring[slot][0] * sc / (double)tot;
-        if (t + tau >= t_end) break;
-        t += tau;
-        T target = (T)sh.ring[slot][1] * tot;
-        if (target >= tot) target = tot * (T)(1.0 - 1e-7);
-        if (active && excl <= target && target < incl) sh.sel[sb] = k;
-        __syncthreads();
-        int i = sh.sel[sb];
-        if (i < 0) i = n - 1;  // no prefix bracket (non-finite rates): stay in bounds
-        sb = (sb + 1) & 3;
+        if (i < 0 || i >= n) i = n - 1;  // no bracket (non-finite rates): stay in bounds
+        // the clock (one thread of the last, partly idle warp; its FP64 latency
+        // overlaps the row below) and dm m_i for the outcome (thread 0)
+        double tn = 0.0, dmmi = 0.0;
+        if (k == kclk) tn = t + (double)fdiv(dr.L, tot);
+        if (k == 0) {
+            sh.sel[1] = -1;
+            dmmi = c.dm * msh[i];
+        }
+        // (2) row i (i meets k) and column i (k meets i) before the event
         const Part<T> pi = parts[i];
-        // row i (i meets k) and column i (k meets i) before the event
-        T Kold, dvik = (T)0;
-        T row = (T)0, colo = (T)0;
+        T Kold, row = (T)0, colo = (T)0;
         if (active) {
-            dvik = pair_dv<T>(c, pk, pi, &Kold);
+            T dvik = pair_dv<T>(pc, pk, pi, &Kold);
             row = Kold * weight<T>(pi, pk);
             colo = Kold * weight<T>(pk, pi);
             dvrow[k] = dvik;
         }
-        if (k == 0) sh.sel[(sb + 1) & 3] = -1;
-        block_scan<T>(row, sh.scan[sb], incl, excl, tot);
-        sb = (sb + 1) & 3;
-        T target2 = (T)sh.ring[slot][2] * tot;
-        if (target2 >= tot) target2 = tot * (T)(1.0 - 1e-7);
-        if (active && excl <= target2 && target2 < incl) sh.sel[sb] = k;
-        __syncthreads();
-        int j = sh.sel[sb];
-        if (j < 0) j = n - 1;
-        sb = (sb + 1) & 3;
+        if (k == kclk) {
+            sh.tnew = tn;
+            sh.stop = tn >= t_end;
+            t = tn;
+        }
+        // (3) choose j by the row's prefix
+        T tot2, unused;
+        int j = block_choose<T, false>(row, (T)0, dr.u2, -1, sh.scan[1], &sh.sel[1], tot2, unused);
+        if (sh.stop) break;  // the event would cross t_end: memoryless, discard
+        if (j < 0 || j >= n) j = n - 1;
+        // (4) outcome and the new cache of i (one thread, FP64 masses)
         if (k == 0) {
             int kind = 0;
-            double mnew = outcome<T>(c, msh[i], msh[j], (double)dvrow[j], sh.ring[slot][3], kind);
+            double mnew = outcome<T>(c, msh[i], msh[j], dmmi, dvrow[j], (double)dr.u3, kind);
             msh[i] = mnew;
-            parts[i] = make_part<T>(c, mnew, A.M[off + i]);
+            parts[i] = make_part<T>(c, mnew, pi.Mv);
             if (logging && ev < A.log_cap) {
                 A.log_ijo[3 * ev] = i;
                 A.log_ijo[3 * ev + 1] = j;
                 A.log_ijo[3 * ev + 2] = kind;
-                A.log_t[ev] = t;
+                A.log_t[ev] = sh.tnew;
                 A.log_m[ev] = mnew;
             }
         }
         __syncthreads();
+        // (5) new row and column i: R_k += r_ki(new) - r_ki(old); R_i afresh
         const Part<T> pn = parts[i];
         if (k == i) pk = pn;
-        T rown = (T)0;
+        rown = (T)0;
         if (active) {
             T Knew;
-            pair_dv<T>(c, pk, pn, &Knew);
+            pair_dv<T>(pc, pk, pn, &Knew);
             rown = Knew * weight<T>(pn, pk);
-            if (k != i) {
-                T coln = Knew * weight<T>(pk, pn);
-                if (sizeof(T) == 8) {
-                    R.add(coln - colo);
-                } else {
-                    R.add(coln);
-                    R.add(-colo);
-                }
-            }
+            if (k != i) R.update(Knew * weight<T>(pk, pn), colo);
         }
-        block_scan<T>(rown, sh.scan[sb], incl, excl, tot);
-        sb = (sb + 1) & 3;
-        if (k == i) R.set(tot);
+        pend = i;
         ++ev;
-        if (ev % reb == 0) rebuild();
+        if (--until_rebuild == 0) {
+            rebuild();
+            pend = -1;
+            rown = (T)0;
+            until_rebuild = reb;
+        }
     }
     if (active) {
         A.m[off + k] = msh[k];
-        if (A.Rdump) A.Rdump[off + k] = R.value() / sc;
+        if (A.Rdump) A.Rdump[off + k] = R.value() / c.sc;
     }
     if (k == 0) {
         A.cell_events[cell] = ev;
@@ -535,7 +698,7 @@ __global__ void k_pair_probe(mcd_disk_params P, double rc, double zc, int64_t n,
     if (threadIdx.x == 0) c = make_cell<T>(P, rc, zc, 1.0, 0.0);
     __syncthreads();
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-        Part<T> a = make_part<T>(c, mi[q], 0.0), b = make_part<T>(c, mj[q], 0.0);
+        Part<T> a = make_part<T>(c, mi[q], (T)0), b = make_part<T>(c, mj[q], (T)0);
         T Kq;
         T d = pair_dv<T>(c, a, b, &Kq);
         dv[q] = (double)d;
@@ -552,7 +715,7 @@ __global__ void k_rate_probe(mcd_disk_params P, double rc, double zc, double V, 
     __shared__ CellK<T> c;
     if (threadIdx.x == 0) c = make_cell<T>(P, rc, zc, V, M[0]);
     __syncthreads();
-    for (int q = threadIdx.x; q < n; q += blockDim.x) parts[q] = make_part<T>(c, m[q], M[q]);
+    for (int q = threadIdx.x; q < n; q += blockDim.x) parts[q] = make_part<T>(c, m[q], (T)(M[q] * c.invVsc));
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         Acc<T> acc;
@@ -568,49 +731,6 @@ __global__ void k_rate_probe(mcd_disk_params P, double rc, double zc, double V, 
         }
         R[i] = acc.value() / c.sc;
     }
-}
-
-// ---- launchers -----------------------------------------------------------------------
-template <class T>
-static cudaError_t collide_impl(mcd_ctx *cx, int from_state, double t_end)
-{
-    int nthr = cx->threads > 0 ? cx->threads : ((cx->n_max + 31) / 32) * 32;
-    if (nthr < 32) nthr = 32;
-    if (nthr > kMaxCell || nthr < cx->n_max) return cudaErrorInvalidValue;
-    size_t smem = (size_t)nthr * (sizeof(Part<T>) + sizeof(double) + sizeof(T));
-    CollideArgs A;
-    A.params = cx->d_params;
-    A.disks = cx->d_disks;
-    A.cell_disk = cx->cell_disk;
-    A.cell_start = cx->cell_start;
-    A.cell_n = cx->cell_n;
-    A.cell_b = cx->cell_b;
-    A.cell_V = cx->cell_V;
-    A.queue = cx->lpt ? cx->queue : nullptr;
-    A.m = cx->m[cx->cur];
-    A.M = cx->M[cx->cur];
-    A.cell_events = cx->cell_events;
-    A.events_total = cx->events_total;
-    A.state = cx->state;
-    A.t_end_fixed = t_end;
-    A.t_end_from_state = from_state;
-    A.seed = cx->seed;
-    A.max_events = cx->max_events;
-    A.rebuild_every = cx->rebuild_every;
-    A.cap_stops = cx->cap_stops;
-    A.status = cx->status;
-    A.Rdump = cx->dump_R ? cx->Rdump : nullptr;
-    A.log_cell = cx->log_cell;
-    A.log_ijo = cx->log_ijo;
-    A.log_t = cx->log_t;
-    A.log_m = cx->log_m;
-    A.log_n = cx->log_n;
-    A.log_cap = mcd_ctx::kLogCap;
-    A.n_cells = cx->C;
-    if (cx->C == 0) return cudaSuccess;
-    k_collide<T><<<(unsigned)cx->C, nthr, smem, cx->stream>>>(A);
-    cx->launches += 1;
-    return cudaGetLastError();
 }
 
 // ---- largest-work-first cell order -------------------------------------------------
@@ -660,19 +780,71 @@ cudaError_t launch_lpt(mcd_ctx *c)
     return cudaGetLastError();
 }
 
+// ---- launchers -----------------------------------------------------------------------
+template <class T>
+static size_t collide_smem(int nthr)
+{
+    return (size_t)nthr * (sizeof(Part<T>) + sizeof(double) + sizeof(T));
+}
+
+template <class T>
+static cudaError_t collide_impl(mcd_ctx *cx, int from_state, double t_end)
+{
+    int nthr = cx->threads > 0 ? cx->threads : ((cx->n_max + 31) / 32) * 32;
+    if (nthr < 32) nthr = 32;
+    if (nthr > kMaxCell || nthr < cx->n_max) return cudaErrorInvalidValue;
+    if (cx->C == 0) return cudaSuccess;
+    const int b = cx->cur;
+    k_cellconst<T><<<(unsigned)((cx->C + 127) / 128), 128, 0, cx->stream>>>(
+        cx->d_params, cx->cell_disk, cx->cell_start, cx->cell_n, cx->cell_b, cx->cell_V, cx->M[b], cx->cellk, cx->C);
+    CollideArgs A;
+    A.params = cx->d_params;
+    A.disks = cx->d_disks;
+    A.cell_disk = cx->cell_disk;
+    A.cell_start = cx->cell_start;
+    A.cell_n = cx->cell_n;
+    A.cell_b = cx->cell_b;
+    A.cell_V = cx->cell_V;
+    A.cellk = cx->cellk;
+    A.queue = cx->lpt ? cx->queue : nullptr;
+    A.m = cx->m[b];
+    A.M = cx->M[b];
+    A.cell_events = cx->cell_events;
+    A.events_total = cx->events_total;
+    A.state = cx->state;
+    A.t_end_fixed = t_end;
+    A.t_end_from_state = from_state;
+    A.seed = cx->seed;
+    A.max_events = cx->max_events;
+    A.rebuild_every = cx->rebuild_every;
+    A.cap_stops = cx->cap_stops;
+    A.status = cx->status;
+    A.Rdump = cx->dump_R ? cx->Rdump : nullptr;
+    A.log_cell = cx->log_cell;
+    A.log_ijo = cx->log_ijo;
+    A.log_t = cx->log_t;
+    A.log_m = cx->log_m;
+    A.log_n = cx->log_n;
+    A.log_cap = mcd_ctx::kLogCap;
+    A.n_cells = cx->C;
+    k_collide<T><<<(unsigned)cx->C, nthr, collide_smem<T>(nthr), cx->stream>>>(A);
+    cx->launches += 2;
+    return cudaGetLastError();
+}
+
 template <class T>
 static cudaError_t prepare_impl()
 {
-    size_t smem = (size_t)kMaxCell * (sizeof(Part<T>) + sizeof(double) + sizeof(T));
-    return cudaFuncSetAttribute(k_collide<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(k_collide<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)collide_smem<T>(kMaxCell));
 }
 
 cudaError_t prepare_collide(mcd_ctx *c)
 {
     cudaError_t e = c->prec == MCD_MIXED ? prepare_impl<float>() : prepare_impl<double>();
     if (e != cudaSuccess) return e;
-    size_t sm = (size_t)1024 * sizeof(Part<double>);
-    e = cudaFuncSetAttribute(k_rate_probe<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = cudaFuncSetAttribute(k_rate_probe<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(1024 * sizeof(Part<double>)));
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_rate_probe<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(1024 * sizeof(Part<float>)));
@@ -701,17 +873,16 @@ cudaError_t launch_rate_probe(const mcd_disk_params &p, int prec, double rc, dou
                               const double *m, const double *M, double *rate, double *R, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    if (prec == MCD_MIXED) {
-        size_t sm = (size_t)n * sizeof(Part<float>);
-        cudaFuncSetAttribute(k_rate_probe<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(1024 * sizeof(Part<float>)));
-        k_rate_probe<float><<<1, 256, sm, s>>>(p, rc, zc, V, n, m, M, rate, R);
-    } else {
-        size_t sm = (size_t)n * sizeof(Part<double>);
-        cudaFuncSetAttribute(k_rate_probe<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(1024 * sizeof(Part<double>)));
-        k_rate_probe<double><<<1, 256, sm, s>>>(p, rc, zc, V, n, m, M, rate, R);
-    }
+    cudaError_t e = cudaFuncSetAttribute(k_rate_probe<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(1024 * sizeof(Part<double>)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_rate_probe<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(1024 * sizeof(Part<float>)));
+    if (e != cudaSuccess) return e;
+    if (prec == MCD_MIXED)
+        k_rate_probe<float><<<1, 256, (size_t)n * sizeof(Part<float>), s>>>(p, rc, zc, V, n, m, M, rate, R);
+    else
+        k_rate_probe<double><<<1, 256, (size_t)n * sizeof(Part<double>), s>>>(p, rc, zc, V, n, m, M, rate, R);
     return cudaGetLastError();
 }
 

@@ -76,7 +76,13 @@ __host__ __device__ inline U4 philox(uint64_t c0, uint64_t c1, uint64_t c2, uint
 // (0,1) from the top 53 bits; the float version rounds that same 53-bit value
 // (relative precision 2^-24 at every magnitude, so log u stays accurate near 0)
 __host__ __device__ inline double u01d(uint64_t x) { return ((double)(x >> 11) + 0.5) * 0x1.0p-53; }
-__host__ __device__ inline float u01f(uint64_t x) { return ((float)(x >> 11) + 0.5f) * 0x1.0p-53f; }
+__host__ __device__ inline float u01f(uint64_t x)
+{
+    // ((x >> 11) + 0.5) 2^-53 from two 32-bit conversions (a 64-bit integer
+    // conversion would run on the slow FP64 unit)
+    uint32_t hi = (uint32_t)(x >> 32), lo = ((uint32_t)x) >> 11;
+    return (float)hi * 0x1.0p-32f + ((float)lo + 0.5f) * 0x1.0p-53f;
+}
 
 // ---- gas disk at (r, z) ------------------------------------------------------
 template <class T>
@@ -149,6 +155,9 @@ constexpr int kRadixBins = 256, kRadixPasses = 8;
 // largest cell population the collide kernel takes (one thread per swarm)
 constexpr int kMaxCell = 512;
 
+// bytes reserved per cell for its gas/drag constants
+constexpr int kCellKBytes = 384;
+
 }  // namespace mcd
 
 // ---- host context ------------------------------------------------------------
@@ -182,6 +191,7 @@ struct mcd_ctx {
     int32_t *cell_n = nullptr;
     double *cell_b = nullptr;  // 6 per cell: r_lo r_hi z_lo z_hi r_c z_c
     double *cell_V = nullptr;
+    unsigned char *cellk = nullptr;  // per-cell constants, kCellKBytes each
 
     int64_t *cell_events = nullptr;
     uint32_t *cell_cost = nullptr;

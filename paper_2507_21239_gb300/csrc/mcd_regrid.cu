@@ -283,21 +283,24 @@ __global__ void __launch_bounds__(1024) k_zone(ZoneArgs A)
     }
     __syncthreads();
     // (2) bitonic sort by (z, id); every compare ascending, i < j, j < nk
-    int64_t P2 = 1;
-    while (P2 < nk) P2 <<= 1;
-    for (int64_t size = 2; size <= P2; size <<= 1) {
-        for (int64_t stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int64_t p = threadIdx.x; p < (P2 >> 1); p += blockDim.x) {
-                int64_t i, j;
-                if (stride == (size >> 1)) {  // first step of a merge: mirror compare
-                    int64_t blk = p / stride, off = p % stride;
-                    i = blk * size + off;
-                    j = blk * size + size - 1 - off;
+    //     (32-bit indices; strides are powers of two, so / and % are shifts)
+    const int nk32 = (int)nk;
+    int lg = 0;
+    while ((1 << lg) < nk32) ++lg;
+    for (int ls = 1; ls <= lg; ++ls) {          // merge size 2^ls
+        for (int lt = ls - 1; lt >= 0; --lt) {   // compare stride 2^lt
+            const int stride = 1 << lt;
+            for (int p = threadIdx.x; p < (1 << (lg - 1)); p += blockDim.x) {
+                int i, j;
+                if (lt == ls - 1) {  // first step of a merge: mirror compare
+                    int blk = p >> lt, off = p & (stride - 1);
+                    i = (blk << ls) + off;
+                    j = (blk << ls) + (1 << ls) - 1 - off;
                 } else {
-                    i = (p / stride) * 2 * stride + p % stride;
+                    i = ((p >> lt) << (lt + 1)) + (p & (stride - 1));
                     j = i + stride;
                 }
-                if (j < nk && zless(skey[j], sid[j], skey[i], sid[i])) {
+                if (j < nk32 && zless(skey[j], sid[j], skey[i], sid[i])) {
                     uint64_t tk = skey[i]; skey[i] = skey[j]; skey[j] = tk;
                     uint32_t ti = sid[i]; sid[i] = sid[j]; sid[j] = ti;
                     uint32_t ts = ssrc[i]; ssrc[i] = ssrc[j]; ssrc[j] = ts;
