@@ -93,6 +93,21 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(sm)}
 
 
+def measured_traffic(name: str):
+    """DRAM bytes per launch recorded from an ncu capture (profiles/traffic.json),
+    or None when the kernel's source changed since the capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[name]
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != rec["sha1"]:
+                return None
+        return float(rec["bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -270,11 +285,11 @@ def run_ours(args):
     fp32_peak = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12  # TFLOP/s
     entries = float(np.sum(n_c * (n_c + 1) / 2) + n_c.mean() * ev_step)
     coll = {"bound": "alu", "achieved": entries * FLOPS_PER_ENTRY / (ph[2] * 1e-3) / 1e12, "peak": fp32_peak,
-            "unit": "TFLOP/s", "traffic": None, "kernel": "k_collide<float>"}
+            "unit": "TFLOP/s", "traffic": measured_traffic("k_collide<float>"), "kernel": "k_collide<float>"}
     reg = {"bound": "hbm", "achieved": REGRID_BYTES * N / (ph[0] * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-           "traffic": None, "kernel": "regrid (k_regrid_keys, k_radix_*, k_zone)"}
+           "traffic": measured_traffic("regrid"), "kernel": "regrid (k_regrid_keys, k_radix_*, k_zone)"}
     tra = {"bound": "hbm", "achieved": TRANSPORT_BYTES * N / (ph[3] * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-           "traffic": None, "kernel": "k_transport<true>"}
+           "traffic": measured_traffic("k_transport<true>"), "kernel": "k_transport<true>"}
     for x in (coll, reg, tra):
         x["frac"] = x["achieved"] / x["peak"]
         x["peak_source"] = src
