@@ -236,6 +236,37 @@ int mcd_pair_probe(const mcd_disk_params *p, int32_t prec, double r_c, double z_
 int mcd_rate_probe(const mcd_disk_params *p, int32_t prec, double r_c, double z_c, double V, int32_t n,
                    const double *m, const double *M, double *rate, double *R, void *cuda_stream);
 
+/*
+ * Regrid of one disk that allocates nothing (the paper has no counterpart;
+ * this is a service entry point).  For callers that cannot call cudaMalloc:
+ * code that runs inside another framework's memory pool or arena, code that
+ * runs inside a caller's CUDA-graph capture or real-time loop where an
+ * allocation would stall or break it, and embedded users with a fixed memory
+ * budget.  It does what mcd_regrid does for one disk, without a context: the
+ * caller passes the particle arrays (n_r * n_z * per_cell of each, device
+ * pointers; ids a permutation of 0..count-1, r = +inf for removed particles)
+ * and receives the arrays in cell order (m_out .. id_out), each cell's first
+ * slot and count (cell_start[n_r*n_z], cell_n[n_r*n_z]), bounds[6 per cell]
+ * (r_lo r_hi z_lo z_hi r_c z_c), volumes V[n_r*n_z], the alive count
+ * (*n_alive) and a device status code (*status: MCD_OK, MCD_ENAN for NaN
+ * positions, MCD_EINVAL for invalid ids, MCD_EEMPTY for an emptied disk), all
+ * device pointers, enqueued on cuda_stream.
+ *
+ * Its scratch (sort keys and values, histograms, tables, status bits) is one
+ * fixed device array of about 2.1 MB that every GPU loading the library holds
+ * until the process exits; hence at most MCD_NOALLOC_MAX_PARTICLES particles
+ * (MCD_EINVAL beyond, and when one radial zone holds more than 14,336).  The
+ * first call on a device looks the array up; make it before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race on
+ * it and must be serialised by the caller.  It calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ */
+#define MCD_NOALLOC_MAX_PARTICLES 65536
+int mcd_regrid_noalloc(const mcd_disk_params *p, const mcd_grid *g, const double *m, const double *M,
+                       const double *r, const double *z, const uint32_t *id, double *m_out, double *M_out,
+                       double *r_out, double *z_out, uint32_t *id_out, int64_t *cell_start, int32_t *cell_n,
+                       double *bounds, double *V, int64_t *n_alive, int32_t *status, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -83,6 +83,7 @@ def lib():
         L.mcd_trace.argtypes = [_vp, C.c_int32]
         L.mcd_trace_read.argtypes = [_vp, _P(C.c_float)]
         L.mcd_get_launch_count.argtypes = [_vp, _P(C.c_int64)]
+        L.mcd_regrid_noalloc.argtypes = [_P(mcd_disk_params), _P(mcd_grid)] + [_vp] * 16 + [_vp]
         L.mcd_sync.argtypes = [_vp]
         L.mcd_free.argtypes = [_vp]
         L.mcd_strerror.argtypes = [C.c_int]
@@ -236,6 +237,18 @@ def mcd_sync(ctx: int) -> int:
 
 def mcd_free(ctx: int):
     _check(lib().mcd_free(ctx), "mcd_free")
+
+
+def mcd_regrid_noalloc(params: dict, grid, inputs, outputs, stream=None):
+    """Context-free regrid of one disk that allocates nothing (device tensors).
+
+    inputs: (m, M, r, z, id); outputs: (m, M, r, z, id, cell_start, cell_n,
+    bounds, V, n_alive, status).  See include/mcd.h for the callers it serves
+    and its limits."""
+    P = mcd_disk_params.from_dict(params)
+    G = mcd_grid(int(grid[0]), int(grid[1]), int(grid[2]), 0)
+    args = [_ptr(t) for t in inputs] + [_ptr(t) for t in outputs]
+    _check(lib().mcd_regrid_noalloc(C.byref(P), C.byref(G), *args, _stream_ptr(stream)), "mcd_regrid_noalloc")
 
 
 def mcd_pair_probe(params: dict, prec: int, rc: float, zc: float, mi, mj, dv, K, stream=None):
