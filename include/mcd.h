@@ -105,12 +105,13 @@ typedef struct mcd_ctx mcd_ctx;
 /* ---- options (mcd_set_option) -------------------------------------------- */
 #define MCD_OPT_MAX_EVENTS 1    /* per cell per collide call; reaching it latches MCD_ETIMEOUT (default 1e7) */
 #define MCD_OPT_CAP_STOPS 2     /* 1: reaching MAX_EVENTS stops the cell without an error (tests) */
-#define MCD_OPT_REBUILD_EVERY 3 /* events between full row-sum rebuilds; 0 = n of the cell (default) */
+#define MCD_OPT_REBUILD_EVERY 3 /* events between full row-sum rebuilds; 0 = 4n of the cell (default) */
 #define MCD_OPT_USE_GRAPH 4     /* 1: mcd_step replays a captured CUDA graph (default 1) */
 #define MCD_OPT_DUMP_R 5        /* 1: keep each particle's row sum after collide (mcd_get_rates) */
 #define MCD_OPT_LOG_CELL 6      /* global cell index whose events are logged; -1 off (default) */
 #define MCD_OPT_LPT 7           /* 1: order cells by descending work estimate (default 1) */
 #define MCD_OPT_THREADS 8       /* threads per cell in collide; 0 = auto */
+#define MCD_OPT_EXCLUSIVE 9     /* 1: one collide CTA per SM, so long event chains share no SM (default 1) */
 
 /*
  * Bytes of device workspace needed for n_disks disks at precision prec.

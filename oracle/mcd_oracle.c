@@ -396,7 +396,7 @@ int orc_collide_cell(const orc_params *P, double rc, double zc, double V, int64_
     if (events_out) *events_out = 0;
     if (n <= 0) return ORC_OK;
     if (P->kernel_mode == 1) V = P->V_const;
-    if (rebuild_every <= 0) rebuild_every = n;
+    if (rebuild_every <= 0) rebuild_every = 4 * n; /* reading: full rebuild every 4n events */
     orc_gas g = orc_gas_at(P, rc, zc);
     double m0 = orc_monomer_mass(P);
     orc_part *pt = (orc_part *)malloc(sizeof(orc_part) * n);

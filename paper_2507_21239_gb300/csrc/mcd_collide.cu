@@ -588,7 +588,7 @@ __global__ void __launch_bounds__(kMaxCell) k_collide(CollideArgs A)
     const uint64_t dcell = (uint64_t)(cell - A.disks[disk].c_off);
     const uint64_t step = (uint64_t)A.state->step;
     const double t_end = A.t_end_from_state ? A.state->t + A.state->dt : A.t_end_fixed;
-    const int64_t reb = A.rebuild_every > 0 ? A.rebuild_every : (int64_t)n;
+    const int64_t reb = A.rebuild_every > 0 ? A.rebuild_every : 4 * (int64_t)n;
     int64_t until_rebuild = reb;  // events left before the next full rebuild
     const bool logging = (cell == A.log_cell);
     const T sc = (T)c.sc;
@@ -781,6 +781,8 @@ cudaError_t launch_lpt(mcd_ctx *c)
 }
 
 // ---- launchers -----------------------------------------------------------------------
+constexpr size_t kExclusiveSmem = 120 * 1024;  // > half of an SM's shared memory
+
 template <class T>
 static size_t collide_smem(int nthr)
 {
@@ -827,7 +829,11 @@ static cudaError_t collide_impl(mcd_ctx *cx, int from_state, double t_end)
     A.log_n = cx->log_n;
     A.log_cap = mcd_ctx::kLogCap;
     A.n_cells = cx->C;
-    k_collide<T><<<(unsigned)cx->C, nthr, collide_smem<T>(nthr), cx->stream>>>(A);
+    // exclusive: request more than half an SM's shared memory so that no two
+    // collide CTAs share an SM (the heaviest cells, launched first, run alone)
+    size_t smem = collide_smem<T>(nthr);
+    if (cx->exclusive && smem < kExclusiveSmem) smem = kExclusiveSmem;
+    k_collide<T><<<(unsigned)cx->C, nthr, smem, cx->stream>>>(A);
     cx->launches += 2;
     return cudaGetLastError();
 }
@@ -835,8 +841,9 @@ static cudaError_t collide_impl(mcd_ctx *cx, int from_state, double t_end)
 template <class T>
 static cudaError_t prepare_impl()
 {
+    size_t need = collide_smem<T>(kMaxCell);
     return cudaFuncSetAttribute(k_collide<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)collide_smem<T>(kMaxCell));
+                                (int)(need > kExclusiveSmem ? need : kExclusiveSmem));
 }
 
 cudaError_t prepare_collide(mcd_ctx *c)
