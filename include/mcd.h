@@ -112,6 +112,9 @@ typedef struct mcd_ctx mcd_ctx;
 #define MCD_OPT_LPT 7           /* 1: order cells by descending work estimate (default 1) */
 #define MCD_OPT_THREADS 8       /* threads per cell in collide; 0 = auto */
 #define MCD_OPT_EXCLUSIVE 9     /* 1: one collide CTA per SM, so long event chains share no SM (default 1) */
+#define MCD_OPT_DV_MATRIX 10    /* 1: MCD_MIXED keeps each cell's dv_ij matrix in shared memory when it fits
+                                   (cells of up to ~230 particles); 0: recompute row i at every event.
+                                   Both give bit-identical results (default 1) */
 
 /*
  * Bytes of device workspace needed for n_disks disks at precision prec.

@@ -500,6 +500,7 @@ int mcd_set_option(mcd_ctx *c, int32_t key, double v)
     case MCD_OPT_LOG_CELL: c->log_cell = (int64_t)v; break;
     case MCD_OPT_LPT: c->lpt = v != 0.0; break;
     case MCD_OPT_EXCLUSIVE: c->exclusive = v != 0.0; break;
+    case MCD_OPT_DV_MATRIX: c->dv_matrix = v != 0.0; break;
     case MCD_OPT_THREADS:
         if (v != 0.0 && (v < c->n_max || v > kMaxCell || ((int)v % 32) != 0)) return MCD_EINVAL;
         c->threads = (int32_t)v;

@@ -11,14 +11,15 @@
 // in shared memory; each thread keeps its own row sum R_k in registers.  The
 // per-cell gas constants come from a separate one-thread-per-cell kernel.
 // One event = a block scan that chooses i (and folds in the previous event's
-// fresh R_i), one kernel entry per thread for row/column i, a block scan
-// that chooses j, the outcome on one thread, and one more kernel entry per
-// thread for the new row/column i: five block barriers.
+// fresh R_i), row/column i before the event (read from the cell's stored dv
+// matrix, or one kernel entry per thread), a block scan whose bracketing lane
+// chooses j and applies the outcome itself, and one kernel entry per thread
+// for the new row/column i: four block barriers.
 //
 // Precision (template T): T = double is the plain FP64 path.  T = float is
 // the mixed path: dv, sigma, K, rates, waiting times and partner choice in
-// FP32; masses and the cell clock in FP64 (kept by one thread, off the
-// critical path, because an FP64 instruction costs ~64 cycles on GB300);
+// FP32; masses and the cell clock in FP64 (touched by one lane per event,
+// because an FP64 instruction costs ~64 cycles on GB300);
 // row sums R_k as compensated FP32 pairs.  Stokes-number differences use a
 // factored difference of cubes over masses split into (hi, lo) FP32 pairs and
 // St itself is carried as a (hi, lo) pair, so close masses lose no digits;
@@ -208,6 +209,17 @@ __device__ __forceinline__ PairK<T> pair_consts(const CellK<T> &c)
     return p;
 }
 
+// Coagulation kernel from a pair's relative velocity: K = pi (a_u + a_v)^2 dv
+// (the constant kernel in the 0D test mode).  The same expression serves the
+// fresh evaluation and the stored-dv path, so both give the same bits.
+template <class T, class C>
+__device__ __forceinline__ T kern_of(const C &c, T au, T av, T dv)
+{
+    if (c.kmode == 1) return c.Kc;
+    T s2 = au + av;
+    return c.pi * s2 * s2 * dv;
+}
+
 // Relative velocity of a pair (symmetric in its arguments bit for bit):
 // Brownian motion, Ormel & Cuzzi (2007) turbulence, radial and azimuthal
 // drift and settling, summed in quadrature.  Returns dv; K via *K.  C is
@@ -249,8 +261,7 @@ __device__ __forceinline__ T pair_dv(const C &c, const Part<T> &u, const Part<T>
         T t0 = c.cbm * (u.im + v.im) + (cls == 1 ? t2 : (cls == 2 ? t3 : (T)0));
         T dv2 = fma(D * D, coef, t0);
         T dv = dv2 > (T)0 ? dv2 * rsqrtf(dv2) : (T)0;
-        T s2 = u.a + v.a;
-        *K = c.pi * s2 * s2 * dv;
+        *K = kern_of<T>(c, u.a, v.a, dv);
         return dv;
     } else {
         if (su & sv) {
@@ -286,8 +297,7 @@ __device__ __forceinline__ T pair_dv(const C &c, const Part<T> &u, const Part<T>
         sz *= qq * qq;
     }
     T dv = msqrt(c.cbm * (u.im + v.im) + tv + rp + sz);
-    T s2 = u.a + v.a;
-    *K = c.pi * s2 * s2 * dv;
+    *K = kern_of<T>(c, u.a, v.a, dv);
     return dv;
 }
 
@@ -306,9 +316,11 @@ __device__ __forceinline__ T weight(const Part<T> &self, const Part<T> &other)
 // the warp totals held one per lane; every warp knows the range [lo, hi) of
 // the prefix it covers, lo of warp w+1 bit-identical to hi of warp w, so
 // exactly one warp brackets the target and finds the element by a ballot.
-// Two barriers; the result is broadcast through shared memory.
+// block_bracket returns the element in that warp's lane 0 and -1 in every
+// other lane (one barrier); block_choose broadcasts it through shared memory
+// (a second barrier).
 template <class V, bool FUSE>
-__device__ __forceinline__ int block_choose(V x, V y, V u, int pend, V *buf, int *sel, V &total, V &ysum)
+__device__ __forceinline__ int block_bracket(V x, V y, V u, int pend, V *buf, V &total, V &ysum)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -349,7 +361,14 @@ __device__ __forceinline__ int block_choose(V x, V y, V u, int pend, V *buf, int
     const V hi = hib + ((pend >= 0 && 32 * w + 31 >= pend) ? Rp : (V)0);
     const unsigned bal = __ballot_sync(FULL, P > target);
     // (a tree scan may leave lane 31's prefix an ulp below hi: then lane 31)
-    if (lane == 0 && lo <= target && target < hi) *sel = 32 * w + __ffs(bal | 0x80000000u) - 1;
+    return (lane == 0 && lo <= target && target < hi) ? 32 * w + __ffs(bal | 0x80000000u) - 1 : -1;
+}
+
+template <class V, bool FUSE>
+__device__ __forceinline__ int block_choose(V x, V y, V u, int pend, V *buf, int *sel, V &total, V &ysum)
+{
+    const int f = block_bracket<V, FUSE>(x, y, u, pend, buf, total, ysum);
+    if (f >= 0) *sel = f;
     __syncthreads();
     return *sel;
 }
@@ -418,9 +437,9 @@ struct Acc<float> {
     __device__ void zero() { s = 0.0f, c = 0.0f; }
     __device__ void add(float x)
     {
-        float t = s + x;
-        float bp = t - s;
-        c += (s - (t - bp)) + (x - bp);
+        float t = __fadd_rn(s, x);
+        float bp = __fsub_rn(t, s);
+        c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp)));
         s = t;
     }
     __device__ void update(float n, float o)
@@ -428,7 +447,7 @@ struct Acc<float> {
         add(n);
         add(-o);
     }
-    __device__ float hi() const { return s + c; }
+    __device__ float hi() const { return __fadd_rn(s, c); }
     __device__ double value() const { return (double)s + (double)c; }
     __device__ void set(float x) { s = x, c = 0.0f; }
 };
@@ -486,16 +505,17 @@ struct CollideArgs {
     unsigned long long *log_n;
     int64_t log_cap;
     int64_t n_cells;
+    int dv_ld;  // row stride of the stored dv matrix (odd; STORE path)
 };
 
 template <class T>
 struct Shared {
     CellK<T> c;
     T scan[2][64];
-    int sel[2];
+    int sel;
     Draw<T> ring[32];
-    double tnew;
-    int stop;
+    double t;  // the cell clock
+    int stop;  // 0 event applied, 1 crossing t_end, 2 no partner bracketed
 };
 
 // per-cell constants: one thread per cell, all SMs (the FP64 gas evaluation is
@@ -512,7 +532,12 @@ __global__ void k_cellconst(const mcd_disk_params *params, const int32_t *cell_d
         make_cell<T>(params[cell_disk[c]], b[4], b[5], cell_V[c], M[cell_start[c]]);
 }
 
-template <class T>
+// STORE (FP32 only): the cell's dv matrix lives in shared memory (row stride
+// A.dv_ld, odd, so a column walk is free of bank conflicts).  Row i before an
+// event is then read, not recomputed, and later full rebuilds sum stored
+// entries; pair_dv is symmetric bit for bit, so the results are those of the
+// recomputing path.
+template <class T, bool STORE>
 __global__ void __launch_bounds__(kMaxCell) k_collide(CollideArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -521,6 +546,8 @@ __global__ void __launch_bounds__(kMaxCell) k_collide(CollideArgs A)
     Part<T> *parts = reinterpret_cast<Part<T> *>(smem_raw);
     double *msh = reinterpret_cast<double *>(parts + nmax);
     T *dvrow = reinterpret_cast<T *>(msh + nmax);
+    T *Dm = dvrow + nmax;  // STORE: dv_kj at Dm[k * ld + j], an ld x ld block
+    const int ld = A.dv_ld;
 
     const int64_t cell = A.queue ? (int64_t)A.queue[blockIdx.x] : (int64_t)blockIdx.x;
     if (cell >= A.n_cells) return;
@@ -530,7 +557,7 @@ __global__ void __launch_bounds__(kMaxCell) k_collide(CollideArgs A)
         if (k == 0) A.cell_events[cell] = 0;
         return;
     }
-    if (n > nmax) {
+    if (n > nmax || (STORE && n > ld)) {
         if (k == 0) atomicOr(A.status, kStBadCell);
         return;
     }
@@ -556,6 +583,7 @@ __global__ void __launch_bounds__(kMaxCell) k_collide(CollideArgs A)
 
     Acc<T> R;
     // R_k = sum_j r_kj in j order; four independent kernel entries in flight
+    // (STORE: the dv entries go to row k of the matrix)
     auto rebuild = [&]() {
         R.zero();
         if (active) {
@@ -564,10 +592,16 @@ __global__ void __launch_bounds__(kMaxCell) k_collide(CollideArgs A)
             for (; sizeof(T) == 4 && j + 4 <= n; j += 4) {
                 T K0, K1, K2, K3;
                 const Part<T> p0 = parts[j], p1 = parts[j + 1], p2 = parts[j + 2], p3 = parts[j + 3];
-                pair_dv<T>(pc, pk, p0, &K0);
-                pair_dv<T>(pc, pk, p1, &K1);
-                pair_dv<T>(pc, pk, p2, &K2);
-                pair_dv<T>(pc, pk, p3, &K3);
+                T d0 = pair_dv<T>(pc, pk, p0, &K0);
+                T d1 = pair_dv<T>(pc, pk, p1, &K1);
+                T d2 = pair_dv<T>(pc, pk, p2, &K2);
+                T d3 = pair_dv<T>(pc, pk, p3, &K3);
+                if (STORE) {
+                    Dm[k * ld + j] = d0;
+                    Dm[k * ld + j + 1] = d1;
+                    Dm[k * ld + j + 2] = d2;
+                    Dm[k * ld + j + 3] = d3;
+                }
                 R.add(K0 * weight<T>(pk, p0));
                 R.add(K1 * weight<T>(pk, p1));
                 R.add(K2 * weight<T>(pk, p2));
@@ -576,10 +610,22 @@ __global__ void __launch_bounds__(kMaxCell) k_collide(CollideArgs A)
             for (; j < n; ++j) {
                 const Part<T> pj = parts[j];
                 T K;
-                pair_dv<T>(pc, pk, pj, &K);
+                T d = pair_dv<T>(pc, pk, pj, &K);
+                if (STORE) Dm[k * ld + j] = d;
                 R.add(K * weight<T>(pk, pj));
             }
         }
+    };
+    // STORE: the same sums from the stored row k (entries written by other
+    // threads since the last barrier are made visible first)
+    auto rebuild_stored = [&]() {
+        __syncthreads();
+        R.zero();
+        if (active)
+            for (int j = 0; j < n; ++j) {
+                const Part<T> pj = parts[j];
+                R.add(kern_of<T>(pc, pk.a, pj.a, Dm[k * ld + j]) * weight<T>(pk, pj));
+            }
     };
     rebuild();
 
@@ -592,8 +638,8 @@ __global__ void __launch_bounds__(kMaxCell) k_collide(CollideArgs A)
     int64_t until_rebuild = reb;  // events left before the next full rebuild
     const bool logging = (cell == A.log_cell);
     const T sc = (T)c.sc;
-    double t = A.state->t;  // the cell clock, kept by the block's last thread
-    const int kclk = blockDim.x - 1;
+    if (k == 0) sh.t = A.state->t;  // (visible after the first ring barrier)
+    const int lane = k & 31;
     int64_t ev = 0;
     int pend = -1;          // swarm whose fresh row sum rides on the next scan
     T rown = (T)0;          // this thread's entry of that row
@@ -608,8 +654,8 @@ __global__ void __launch_bounds__(kMaxCell) k_collide(CollideArgs A)
         //     the previous event's R_i (sum of its new row) is folded in here
         T val = (active && k != pend) ? (T)R.hi() : (T)0;
         T tot, Rp;
-        if (k == 0) sh.sel[0] = -1;
-        int i = block_choose<T, true>(val, rown, dr.u1, pend, sh.scan[0], &sh.sel[0], tot, Rp);
+        if (k == 0) sh.sel = -1;
+        int i = block_choose<T, true>(val, rown, dr.u1, pend, sh.scan[0], &sh.sel, tot, Rp);
         if (pend >= 0 && k == pend) R.set(Rp);
         if (!(tot > (T)0)) break;
         if (ev >= A.max_events) {
@@ -617,62 +663,76 @@ __global__ void __launch_bounds__(kMaxCell) k_collide(CollideArgs A)
             break;
         }
         if (i < 0 || i >= n) i = n - 1;  // no bracket (non-finite rates): stay in bounds
-        // the clock (one thread of the last, partly idle warp; its FP64 latency
-        // overlaps the row below) and dm m_i for the outcome (thread 0)
-        double tn = 0.0, dmmi = 0.0;
-        if (k == kclk) tn = t + (double)fdiv(dr.L, tot);
-        if (k == 0) {
-            sh.sel[1] = -1;
-            dmmi = c.dm * msh[i];
+        // the lane that brackets j applies the event (lane 0 of some warp): every
+        // warp's lane 0 reads m_i and forms dm m_i ahead (FP64 latency, off the path)
+        double mi = 0.0, dmmi = 0.0;
+        if (lane == 0) {
+            mi = msh[i];
+            dmmi = c.dm * mi;
         }
+        if (k == 0) sh.stop = 2;
         // (2) row i (i meets k) and column i (k meets i) before the event
         const Part<T> pi = parts[i];
         T Kold, row = (T)0, colo = (T)0;
         if (active) {
-            T dvik = pair_dv<T>(pc, pk, pi, &Kold);
+            if (STORE) {
+                Kold = kern_of<T>(pc, pk.a, pi.a, Dm[i * ld + k]);
+            } else {
+                T dvik = pair_dv<T>(pc, pk, pi, &Kold);
+                dvrow[k] = dvik;
+            }
             row = Kold * weight<T>(pi, pk);
             colo = Kold * weight<T>(pk, pi);
-            dvrow[k] = dvik;
         }
-        if (k == kclk) {
-            sh.tnew = tn;
-            sh.stop = tn >= t_end;
-            t = tn;
-        }
-        // (3) choose j by the row's prefix
+        // (3) choose j by the row's prefix; (4) the lane that finds j advances
+        //     the clock and, unless the event would cross t_end (memoryless:
+        //     discarded), applies the outcome and the new cache of i (FP64 masses)
         T tot2, unused;
-        int j = block_choose<T, false>(row, (T)0, dr.u2, -1, sh.scan[1], &sh.sel[1], tot2, unused);
-        if (sh.stop) break;  // the event would cross t_end: memoryless, discard
-        if (j < 0 || j >= n) j = n - 1;
-        // (4) outcome and the new cache of i (one thread, FP64 masses)
-        if (k == 0) {
-            int kind = 0;
-            double mnew = outcome<T>(c, msh[i], msh[j], dmmi, dvrow[j], (double)dr.u3, kind);
-            msh[i] = mnew;
-            parts[i] = make_part<T>(c, mnew, pi.Mv);
-            if (logging && ev < A.log_cap) {
-                A.log_ijo[3 * ev] = i;
-                A.log_ijo[3 * ev + 1] = j;
-                A.log_ijo[3 * ev + 2] = kind;
-                A.log_t[ev] = sh.tnew;
-                A.log_m[ev] = mnew;
+        int j = block_bracket<T, false>(row, (T)0, dr.u2, -1, sh.scan[1], tot2, unused);
+        if (j >= 0) {
+            if (j >= n) j = n - 1;  // (lane 31 fallback in a partly idle warp)
+            const double tn = sh.t + (double)fdiv(dr.L, tot);
+            const int stop = tn >= t_end;
+            if (!stop) {
+                int kind = 0;
+                double mnew = outcome<T>(c, mi, msh[j], dmmi, STORE ? Dm[i * ld + j] : dvrow[j], (double)dr.u3, kind);
+                msh[i] = mnew;
+                parts[i] = make_part<T>(c, mnew, pi.Mv);
+                sh.t = tn;
+                if (logging && ev < A.log_cap) {
+                    A.log_ijo[3 * ev] = i;
+                    A.log_ijo[3 * ev + 1] = j;
+                    A.log_ijo[3 * ev + 2] = kind;
+                    A.log_t[ev] = tn;
+                    A.log_m[ev] = mnew;
+                }
             }
+            sh.stop = stop;
         }
         __syncthreads();
+        if (sh.stop) {
+            // no lane bracketed j: the row's prefix sums are not finite
+            if (sh.stop == 2 && k == 0) atomicOr(A.status, kStNaN);
+            break;
+        }
         // (5) new row and column i: R_k += r_ki(new) - r_ki(old); R_i afresh
         const Part<T> pn = parts[i];
         if (k == i) pk = pn;
         rown = (T)0;
         if (active) {
             T Knew;
-            pair_dv<T>(pc, pk, pn, &Knew);
+            T dvn = pair_dv<T>(pc, pk, pn, &Knew);
+            if (STORE) {
+                Dm[i * ld + k] = dvn;
+                Dm[k * ld + i] = dvn;
+            }
             rown = Knew * weight<T>(pn, pk);
             if (k != i) R.update(Knew * weight<T>(pk, pn), colo);
         }
         pend = i;
         ++ev;
         if (--until_rebuild == 0) {
-            rebuild();
+            if (STORE) rebuild_stored(); else rebuild();
             pend = -1;
             rown = (T)0;
             until_rebuild = reb;
@@ -833,22 +893,52 @@ static cudaError_t collide_impl(mcd_ctx *cx, int from_state, double t_end)
     // collide CTAs share an SM (the heaviest cells, launched first, run alone)
     size_t smem = collide_smem<T>(nthr);
     if (cx->exclusive && smem < kExclusiveSmem) smem = kExclusiveSmem;
-    k_collide<T><<<(unsigned)cx->C, nthr, smem, cx->stream>>>(A);
+    // FP32: the dv matrix (ld x ld, ld = n_max rounded up to odd) when it fits
+    const int ld = cx->n_max | 1;
+    const size_t smem_store = collide_smem<T>(nthr) + (size_t)ld * ld * sizeof(T);
+    const bool store = sizeof(T) == 4 && cx->dv_matrix && smem_store <= (size_t)cx->smem_optin;
+    A.dv_ld = ld;
+    if constexpr (sizeof(T) == 4)
+        if (store) {
+            k_collide<T, true><<<(unsigned)cx->C, nthr, smem_store > smem ? smem_store : smem, cx->stream>>>(A);
+            cx->launches += 2;
+            return cudaGetLastError();
+        }
+    k_collide<T, false><<<(unsigned)cx->C, nthr, smem, cx->stream>>>(A);
     cx->launches += 2;
     return cudaGetLastError();
 }
 
+// the dynamic shared memory each variant may request; for the stored-matrix
+// variant, what the device lets a block opt in to beyond its static part
 template <class T>
-static cudaError_t prepare_impl()
+static cudaError_t prepare_impl(mcd_ctx *c)
 {
     size_t need = collide_smem<T>(kMaxCell);
-    return cudaFuncSetAttribute(k_collide<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(need > kExclusiveSmem ? need : kExclusiveSmem));
+    cudaError_t e = cudaFuncSetAttribute(k_collide<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(need > kExclusiveSmem ? need : kExclusiveSmem));
+    c->smem_optin = 0;
+    if constexpr (sizeof(T) != 4) {
+        return e;
+    } else {
+        if (e != cudaSuccess) return e;
+        int dev = 0, optin = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+            return e;
+        cudaFuncAttributes fa;
+        if ((e = cudaFuncGetAttributes(&fa, k_collide<T, true>)) != cudaSuccess) return e;
+        const int dyn = optin - (int)fa.sharedSizeBytes;
+        if (dyn <= 0) return cudaSuccess;
+        e = cudaFuncSetAttribute(k_collide<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        if (e == cudaSuccess) c->smem_optin = dyn;
+        return e;
+    }
 }
 
 cudaError_t prepare_collide(mcd_ctx *c)
 {
-    cudaError_t e = c->prec == MCD_MIXED ? prepare_impl<float>() : prepare_impl<double>();
+    cudaError_t e = c->prec == MCD_MIXED ? prepare_impl<float>(c) : prepare_impl<double>(c);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_rate_probe<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(1024 * sizeof(Part<double>)));

@@ -408,3 +408,37 @@ def test_graph_replay_equals_direct_launches(prec):
     assert sa.events == sb.events and sa.step == sb.step == 5 and sa.t == sb.t
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("grid,reb", [((8, 4, 30), 0), ((4, 2, 57), 7), ((1, 1, 200), 0), ((2, 2, 224), 13)])
+def test_dv_matrix_equals_recompute(grid, reb):
+    """Collide with each cell's dv matrix kept in shared memory reaches the same
+    bits as the path that recomputes row i at every event.  Mid-run state, so
+    sticking, erosion and fragmentation all occur; reb > 0 also runs the full
+    rebuilds from stored entries; 224 particles per cell is the largest matrix
+    that fits."""
+    P = W.benchmark_disk()
+    N = grid[0] * grid[1] * grid[2]
+    m, r, z = W.midrun_state(P, N, seed=3)
+    # squeezed to 1..6 AU: ~10^3..10^4 events per cell and year
+    r2 = P["r_in"] + (r - P["r_in"]) * (5.0 * AU / (P["r_out"] - P["r_in"]))
+    r, z = r2, z * (r2 / r) ** 1.25
+    out = []
+    for mat in (1, 0):
+        d = _make_ctx(P, grid, seed=4, prec=mcd.MCD_MIXED)
+        p = d.particles()
+        mcd.mcd_set_particles(d.ctx, 0, m, p["M"], r, z, p["id"])
+        for key, v in ((mcd.MCD_OPT_DV_MATRIX, mat), (mcd.MCD_OPT_REBUILD_EVERY, reb), (mcd.MCD_OPT_DUMP_R, 1)):
+            mcd.mcd_set_option(d.ctx, key, v)
+        for _ in range(3):
+            d.step(YR)
+        assert mcd.mcd_sync(d.ctx) == mcd.MCD_OK
+        R = np.zeros(N)
+        mcd.mcd_get_rates(d.ctx, 0, R)
+        out.append((d.particles(), d.stats().events, R))
+        d.close()
+    (x, ea, Ra), (y, eb, Rb) = out
+    assert ea == eb and ea > 50
+    for key in ("m", "r", "z", "id"):
+        assert np.array_equal(x[key], y[key]), key
+    assert np.array_equal(Ra, Rb)
