@@ -50,8 +50,8 @@ struct CellK {
     T Cep, Cst, cm, asw, vg2, Se, cbm, e4, e1, oz2, Kc, pi;
     T Cep_lo, Cst_lo, cm_lo;                         // low parts (FP32 path)
     T msw_h, msw_l, meta_h, meta_l, mone_h, mone_l;  // mass thresholds as hi + lo
-    T invVsc_t, dm_t, vfrag_t;
-    int32_t kmode, settle;
+    T invVsc_t, dm_t, vfrag_t, m0_t, fe_t;
+    int32_t kmode, settle, fe_zero;
     double m_sw, m_eta, m_one, m0, V, sc, invVsc, vfrag, ratio, chi, dm, fe, cm_d;
 };
 static_assert(sizeof(CellK<double>) <= kCellKBytes && sizeof(CellK<float>) <= kCellKBytes, "cell constants");
@@ -106,6 +106,7 @@ __device__ CellK<T> make_cell(const mcd_disk_params &P, double rc, double zc, do
     c.invVsc = c.V > 0.0 ? c.sc / c.V : 0.0;
     c.invVsc_t = (T)c.invVsc;
     c.m0 = monomer_mass(P);
+    c.m0_t = (T)c.m0;
     c.vfrag = P.v_frag;
     c.vfrag_t = (T)P.v_frag;
     c.ratio = P.erosion_ratio;
@@ -113,7 +114,36 @@ __device__ CellK<T> make_cell(const mcd_disk_params &P, double rc, double zc, do
     c.dm = P.dm_group;
     c.dm_t = (T)P.dm_group;
     c.fe = 2.0 - P.frag_xi;
+    c.fe_t = (T)c.fe;
+    c.fe_zero = fabs(c.fe) < 1e-12;
     return c;
+}
+
+// (float)m and (float)(m - (double)(float)m) for a double in [2^-74, 2^126)
+// (mass_splits), on the integer unit: an f64 <-> f32 conversion costs ~70 cycles of
+// latency on GB300, this whole split ~40.  The 53-bit significand is rounded to
+// 24 bits, to nearest with ties to even (a carry rolls into the exponent
+// field), and the remainder, exact as a signed 30-bit integer, is rounded to
+// float and scaled by the exponent.  (No fallback branch: the compiler would
+// predicate it and wait for the FP64 route.)
+__device__ __forceinline__ bool mass_splits(double m) { return (unsigned)(__double_as_longlong(m) >> 52) - 949u <= 200u; }
+__device__ __forceinline__ void split_f64(double m, float &h, float &l)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(m);
+    const unsigned lo = (unsigned)b, E = (unsigned)(b >> 52);
+    const unsigned up = ((lo >> 28) & 1u) & (((lo & 0x0FFFFFFFu) != 0u) | ((lo >> 29) & 1u));
+    h = __uint_as_float((unsigned)(b >> 29) - (896u << 23) + up);  // exponent rebiased mod 2^32
+    const int D = (int)(lo & 0x1FFFFFFFu) - (int)(up << 29);
+    l = __int2float_rn(D) * __uint_as_float((E - 948u) << 23);  // D 2^(E-1075), E-1075 >= -126
+}
+
+// (double)f for a positive normal float, on the integer unit
+__device__ __forceinline__ double f2d_pos(float f)
+{
+    const unsigned x = __float_as_uint(f);
+    if ((x >> 23) - 1u >= 254u) return (double)f;  // zero, subnormal, inf, NaN or negative
+    return __longlong_as_double((long long)((((unsigned long long)(x >> 23) + 896ull) << 52) |
+                                            ((unsigned long long)(x & 0x7FFFFFu) << 29)));
 }
 
 // (ah, al) < (bh, bl) for normalised hi + lo pairs
@@ -144,12 +174,13 @@ __device__ __forceinline__ Part<double> make_part<double>(const CellK<double> &c
     return q;
 }
 
-// FP32 path: one FP64 instruction (the lo part of the mass), the rest FP32.
+// FP32 path: no FP64 instruction (masses within the split's range).
 template <>
 __device__ __forceinline__ Part<float> make_part<float>(const CellK<float> &c, double m, float Mv)
 {
     Part<float> q;
-    float mh = (float)m, ml = (float)(m - (double)mh);
+    float mh, ml;
+    split_f64(m, mh, ml);
     q.mh = mh;
     q.ml = ml;
     bool stk = !pair_lt(mh, ml, c.msw_h, c.msw_l);
@@ -342,6 +373,7 @@ __device__ __forceinline__ int block_bracket(V x, V y, V u, int pend, V *buf, V 
     V bs = bt;
 #pragma unroll
     for (int o = 1; o < kMaxCell / 32; o <<= 1) {
+        if (o >= nw) break;  // (block-uniform) log2(nw) rounds
         V a = __shfl_up_sync(FULL, bs, o);
         if (lane >= o) bs += a;
         if (FUSE) by += __shfl_xor_sync(FULL, by, o);
@@ -374,48 +406,65 @@ __device__ __forceinline__ int block_choose(V x, V y, V u, int pend, V *buf, int
 }
 
 // ---- outcomes ----------------------------------------------------------------
-// mass-weighted draw on [m0, mmax] from n(m) ~ m^-xi, e = 2 - xi:
-// m = m0 [1 + u ((mmax/m0)^e - 1)]^(1/e), in expm1/log1p form (relative
-// precision kept when mmax is close to m0)
-__device__ double frag_draw(double m0, double fe, double mmax, double u, bool fp32)
-{
-    if (mmax <= m0) return m0;
-    double m;
-    if (fp32) {
-        float L = logf(__fdividef((float)mmax, (float)m0)), e = (float)fe;
-        m = fabs(fe) < 1e-12 ? m0 * (double)expf((float)u * L)
-                             : m0 * (double)expf(log1pf((float)u * expm1f(e * L)) / e);
-    } else {
-        double L = log(mmax / m0);
-        m = fabs(fe) < 1e-12 ? m0 * exp(u * L) : m0 * exp(log1p(u * expm1(fe * L)) / fe);
-    }
-    return fmin(fmax(m, m0), mmax);
-}
-
-// order of positive finite doubles through their bit patterns (integer unit)
+// order of positive finite doubles through their bit patterns (integer unit);
+// a negative value (sign bit set) orders below every positive one
 __device__ __forceinline__ bool dgt(double a, double b) { return __double_as_longlong(a) > __double_as_longlong(b); }
 
-// new mass of representative i after meeting a particle of swarm j; dmmi is
-// dm m_i (0 when grouping is off), computed ahead by the caller
+// mass-weighted draw on [m0, mmax] from n(m) ~ m^-xi, e = 2 - xi:
+// m = m0 [1 + u ((mmax/m0)^e - 1)]^(1/e), in expm1/log1p form (relative
+// precision kept when mmax is close to m0); the clamp to [m0, mmax] by dgt
 template <class T>
-__device__ double outcome(const CellK<T> &c, double mi, double mj, double dmmi, T dv, double u3, int &kind)
+struct Frag;
+template <>
+struct Frag<double> {
+    static __device__ double draw(const CellK<double> &c, double mmax, double, double u)
+    {
+        if (!dgt(mmax, c.m0)) return c.m0;
+        const double L = log(mmax / c.m0);
+        double m = c.fe_zero ? c.m0 * exp(u * L) : c.m0 * exp(log1p(u * expm1(c.fe * L)) / c.fe);
+        m = dgt(c.m0, m) ? c.m0 : m;
+        return dgt(m, mmax) ? mmax : m;
+    }
+};
+// FP32 path: L and the draw in FP32 from the float images of mmax (its cache
+// hi part) and m0; m0 times the draw in FP64
+template <>
+struct Frag<float> {
+    static __device__ double draw(const CellK<float> &c, double mmax, float mmax_h, float u)
+    {
+        if (!dgt(mmax, c.m0)) return c.m0;
+        const float L = logf(__fdividef(mmax_h, c.m0_t)), e = c.fe_t;
+        const float f = c.fe_zero ? expf(u * L) : expf(log1pf(u * expm1f(e * L)) / e);
+        double m = c.m0 * f2d_pos(f);
+        m = dgt(c.m0, m) ? c.m0 : m;
+        return dgt(m, mmax) ? mmax : m;
+    }
+};
+
+// new mass of representative i after meeting a particle of swarm j; dmmi is
+// dm m_i (0 when grouping is off), computed ahead by the caller; mih, mjh the
+// hi parts of the masses (FP32 path)
+template <class T>
+__device__ __forceinline__ double outcome(const CellK<T> &c, double mi, double mj, T mih, T mjh, double dmmi, T dv,
+                                          T u3, int &kind)
 {
-    double gain = dgt(dmmi, mj) ? dmmi : mj;  // N_g m_j
+    const double gain = dgt(dmmi, mj) ? dmmi : mj;  // N_g m_j
     if (c.kmode == 1 || dv < (sizeof(T) == 4 ? (T)c.vfrag_t : (T)c.vfrag)) {
         kind = 0;
         return mi + gain;
     }
-    double big = dgt(mi, mj) ? mi : mj, small = dgt(mi, mj) ? mj : mi;
+    const bool igt = dgt(mi, mj);
+    const double big = igt ? mi : mj, small = igt ? mj : mi;
     if (big >= c.ratio * small) {
         kind = 2;
         if (!dgt(mj, mi)) {
-            double mn = mi - c.chi * gain;
-            return mn > c.m0 ? mn : c.m0;
+            const double mn = mi - c.chi * gain;
+            return dgt(mn, c.m0) ? mn : c.m0;
         }
-        return frag_draw(c.m0, c.fe, mi, u3, sizeof(T) == 4);
+        return Frag<T>::draw(c, mi, mih, u3);
     }
     kind = 1;
-    return frag_draw(c.m0, c.fe, big, u3, sizeof(T) == 4);
+    return Frag<T>::draw(c, big, igt ? mih : mjh, u3);
 }
 
 // ---- accumulators: FP64 sum, or a compensated FP32 pair ------------------------
@@ -575,6 +624,9 @@ __global__ void __launch_bounds__(kMaxCell) k_collide(CollideArgs A)
     Part<T> pk;
     if (active) {
         double mk = A.m[off + k];
+        // FP32 path: every mass the event loop can reach lies between the
+        // monomer mass and the disk's dust mass, inside the split's range
+        if (sizeof(T) == 4 && !mass_splits(mk)) atomicOr(A.status, kStBadCell);
         msh[k] = mk;
         pk = make_part<T>(c, mk, (T)(A.M[off + k] * c.invVsc));
         parts[k] = pk;
@@ -691,13 +743,17 @@ __global__ void __launch_bounds__(kMaxCell) k_collide(CollideArgs A)
         int j = block_bracket<T, false>(row, (T)0, dr.u2, -1, sh.scan[1], tot2, unused);
         if (j >= 0) {
             if (j >= n) j = n - 1;  // (lane 31 fallback in a partly idle warp)
+            // the clock, the outcome and the new cache are independent chains;
+            // only the stores wait for the crossing test
             const double tn = sh.t + (double)fdiv(dr.L, tot);
+            int kind = 0;
+            const double mnew = outcome<T>(c, mi, msh[j], pi.mh, parts[j].mh, dmmi, STORE ? Dm[i * ld + j] : dvrow[j],
+                                           dr.u3, kind);
+            const Part<T> pnew = make_part<T>(c, mnew, pi.Mv);
             const int stop = tn >= t_end;
             if (!stop) {
-                int kind = 0;
-                double mnew = outcome<T>(c, mi, msh[j], dmmi, STORE ? Dm[i * ld + j] : dvrow[j], (double)dr.u3, kind);
                 msh[i] = mnew;
-                parts[i] = make_part<T>(c, mnew, pi.Mv);
+                parts[i] = pnew;
                 sh.t = tn;
                 if (logging && ev < A.log_cap) {
                     A.log_ijo[3 * ev] = i;
