@@ -146,6 +146,21 @@ __device__ __forceinline__ double f2d_pos(float f)
                                             ((unsigned long long)(x & 0x7FFFFFu) << 29)));
 }
 
+// MUFU base-2 exponential and logarithm (flush-to-zero forms; arguments here
+// are normal)
+__device__ __forceinline__ float ex2_mufu(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_mufu(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // (ah, al) < (bh, bl) for normalised hi + lo pairs
 __device__ __forceinline__ bool pair_lt(float ah, float al, float bh, float bl) { return ah < bh || (ah == bh && al < bl); }
 
@@ -189,11 +204,13 @@ __device__ __forceinline__ Part<float> make_part<float>(const CellK<float> &c, d
     // root plus one Newton step on the residual x - a0^3 taken exactly
     float xh = c.cm * mh;
     float xl = fmaf(c.cm, mh, -xh) + c.cm * ml + c.cm_lo * mh;
-    float a0 = exp2f(__log2f(xh) * (1.0f / 3.0f));  // refined to full precision below
+    const float l3 = lg2_mufu(xh) * (1.0f / 3.0f);
+    float a0 = ex2_mufu(l3);        // refined to full precision below
+    const float ia = ex2_mufu(-l3);  // 1/a0 to a few ulp, alongside a0
     float p2 = a0 * a0, p2e = fmaf(a0, a0, -p2);     // a0^2 = p2 + p2e
     float p3 = p2 * a0, p3e = fmaf(p2, a0, -p3);     // p2 a0 = p3 + p3e
     float res = (((xh - p3) - p3e) - p2e * a0) + xl;  // x - a0^3
-    float alo = res * __fdividef(1.0f, 3.0f * p2);
+    float alo = res * (ia * ia * (1.0f / 3.0f));      // res / (3 a0^2): a correction, few digits needed
     q.a = a0;
     float Sh, Se;
     if (stk) {  // S = Cst a^2 = Cst (p2 + p2e + 2 a0 alo)
@@ -280,9 +297,12 @@ __device__ __forceinline__ T pair_dv(const C &c, const Part<T> &u, const Part<T>
         D = (su & sv) ? D_st : ((su | sv) ? D_mx : D_ep);
         T s = S1 + S2;
         T g1 = fdiv(c.vg2 * fma(S1, S2, c.Se * s), s * (S1 + c.Se) * (S2 + c.Se));  // regime I: D^2 g1
-        T eps = fdiv(S2, S1), ope = (T)1 + eps, yae = (T)kYA + eps;
-        T last = fdiv((T)2 * (yae * (T)(1.0 / (1.0 + kYA)) + eps * eps * eps), ope * yae);
-        T t2 = c.vg2 * S1 * (((T)(2.0 * kYA) - ope) + last);
+        // regime II with eps = S2/S1 cleared from the fractions (one division):
+        // vg2 [(2 y_a - 1) S1 - S2 + 2((y_a S1 + S2) S1^2/(1+y_a) + S2^3) / ((S1+S2)(y_a S1 + S2))],
+        // every term positive (S2 <= S1, S1 < 1 where this regime applies)
+        T A1 = fma((T)kYA, S1, S2);
+        T num = fma(A1 * (S1 * S1), (T)(1.0 / (1.0 + kYA)), S2 * S2 * S2);
+        T t2 = c.vg2 * (fma((T)(2.0 * kYA - 1.0), S1, -S2) + fdiv((T)2 * num, s * A1));
         T t3 = c.vg2 * (u.q + v.q);
         T pp = u.p * v.p;
         T om = fma(-u.S, v.S, (T)1) - (mul_rn(u.S, v.Sl) + mul_rn(u.Sl, v.S));
