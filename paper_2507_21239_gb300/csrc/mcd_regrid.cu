@@ -147,34 +147,50 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_parts(uint32_t *part, int
     }
 }
 
+constexpr size_t kScatterStage = (size_t)kRadixTile * (sizeof(uint64_t) + sizeof(uint32_t));
+
+// One tile: rank every key within its digit (warp match, then a prefix over
+// warps), stage the tile in shared memory in digit order, and write it out
+// run by run, so consecutive threads store consecutive addresses of a digit's
+// destination range.
 __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const DiskDev *disks, const int32_t *tile_disk,
                                                                  const uint64_t *ksrc, const uint32_t *vsrc,
                                                                  uint64_t *kdst, uint32_t *vdst, int shift,
                                                                  const uint32_t *hist, const uint32_t *part)
 {
     __shared__ uint32_t wcnt[kRadixThreads / 32][kRadixBins];
-    __shared__ uint32_t toff[kRadixBins];
+    __shared__ uint32_t toff[kRadixBins], loff[kRadixBins], wsum[32];
+    extern __shared__ __align__(16) unsigned char stage_raw[];  // kScatterStage bytes
+    uint64_t *skey = reinterpret_cast<uint64_t *>(stage_raw);
+    uint32_t *sval = reinterpret_cast<uint32_t *>(skey + kRadixTile);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int64_t t = blockIdx.x;
     const DiskDev D = disks[tile_disk[t]];
     int64_t start = D.p_off + (t - D.t_off) * kRadixTile;
     int64_t end = min(start + kRadixTile, D.p_off + D.n0);
+    const int nvalid = (int)(end - start);
     {
         int64_t hi = hidx(D, t, threadIdx.x);
         toff[threadIdx.x] = hist[hi] + part[hi / kScanBlock];
     }
     for (int q = threadIdx.x; q < (kRadixThreads / 32) * kRadixBins; q += kRadixThreads) (&wcnt[0][0])[q] = 0;
-    __syncthreads();
+    // every load of the tile issued before the first use
     uint64_t kk[kRadixItems];
     uint32_t vv[kRadixItems], rk[kRadixItems];
     int dg[kRadixItems];
+#pragma unroll
+    for (int it = 0; it < kRadixItems; ++it) {
+        const int lq = w * (32 * kRadixItems) + it * 32 + lane;
+        const bool ok = lq < nvalid;
+        kk[it] = ok ? ksrc[start + lq] : 0;
+        vv[it] = ok ? vsrc[start + lq] : 0;
+    }
+    __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
     for (int it = 0; it < kRadixItems; ++it) {
-        int64_t q = start + (int64_t)w * (32 * kRadixItems) + it * 32 + lane;
-        bool ok = q < end;
-        kk[it] = ok ? ksrc[q] : 0;
-        vv[it] = ok ? vsrc[q] : 0;
+        const int lq = w * (32 * kRadixItems) + it * 32 + lane;
+        const bool ok = lq < nvalid;
         int digit = ok ? (int)((kk[it] >> shift) & 255) : 256;
         dg[it] = digit;
         unsigned peers = __match_any_sync(0xffffffffu, digit);
@@ -189,8 +205,10 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const DiskDev *
         __syncwarp();
     }
     __syncthreads();
+    // per digit: offsets of the warps within it, and the tile's count of it
+    uint32_t cnt;
     {
-        int b = threadIdx.x;
+        const int b = threadIdx.x;
         uint32_t run = 0;
 #pragma unroll
         for (int ww = 0; ww < kRadixThreads / 32; ++ww) {
@@ -198,15 +216,40 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const DiskDev *
             wcnt[ww][b] = run;
             run += c;
         }
+        cnt = run;
+    }
+    // exclusive scan of the digit counts: the digit's first slot in the staged tile
+    {
+        uint32_t v = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        if (lane == 31) wsum[w] = v;
+        __syncthreads();
+        uint32_t off = 0;
+#pragma unroll
+        for (int ww = 0; ww < kRadixThreads / 32; ++ww) off += ww < w ? wsum[ww] : 0u;
+        loff[threadIdx.x] = off + v - cnt;
     }
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < kRadixItems; ++it) {
         if (dg[it] < 256) {
-            uint32_t pos = toff[dg[it]] + wcnt[w][dg[it]] + rk[it];
-            kdst[pos] = kk[it];
-            vdst[pos] = vv[it];
+            const uint32_t pos = loff[dg[it]] + wcnt[w][dg[it]] + rk[it];
+            skey[pos] = kk[it];
+            sval[pos] = vv[it];
         }
+    }
+    __syncthreads();
+    // write out in staged order: position p of digit d goes to toff[d] + (p - loff[d])
+    for (int p = threadIdx.x; p < nvalid; p += kRadixThreads) {
+        const uint64_t k = skey[p];
+        const int d = (int)((k >> shift) & 255);
+        const uint32_t g = toff[d] + ((uint32_t)p - loff[d]);
+        kdst[g] = k;
+        vdst[g] = sval[p];
     }
 }
 
@@ -224,10 +267,15 @@ __global__ void k_count_alive(const DiskDev *disks, int nd, const uint64_t *key,
     if (lo == 0 && D.n0 > 0) atomicOr(status, kStEmpty);
 }
 
-__device__ __forceinline__ bool zless(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib)
+// a zone element in shared memory: (z key lo, z key hi, id, source slot)
+__device__ __forceinline__ uint64_t el_key(const uint4 &e) { return ((uint64_t)e.y << 32) | e.x; }
+__device__ __forceinline__ bool zless(const uint4 &a, const uint4 &b)
 {
-    return ka < kb || (ka == kb && ia < ib);
+    const uint64_t ka = el_key(a), kb = el_key(b);
+    return ka < kb || (ka == kb && a.z < b.z);
 }
+
+constexpr int kZoneThreads = 512;  // two zones per SM
 
 struct ZoneArgs {
     const mcd_disk_params *params;
@@ -246,7 +294,7 @@ struct ZoneArgs {
     int32_t *status;
 };
 
-__global__ void __launch_bounds__(1024) k_zone(ZoneArgs A)
+__global__ void __launch_bounds__(kZoneThreads, 2) k_zone(ZoneArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int zg = blockIdx.x;
@@ -259,9 +307,7 @@ __global__ void __launch_bounds__(1024) k_zone(ZoneArgs A)
     const int64_t nk = base + (k < rem ? 1 : 0);
     const int64_t zs = k * base + (k < rem ? k : rem);
     const int64_t c0 = D.c_off + k * nz;
-    uint64_t *skey = reinterpret_cast<uint64_t *>(smem_raw);
-    uint32_t *sid = reinterpret_cast<uint32_t *>(skey + nk);
-    uint32_t *ssrc = sid + nk;
+    uint4 *el = reinterpret_cast<uint4 *>(smem_raw);
     const uint64_t *rk = A.rkey + D.p_off;
 
     // (1) load this zone's (z, id, source) triples
@@ -277,37 +323,55 @@ __global__ void __launch_bounds__(1024) k_zone(ZoneArgs A)
             atomicOr(A.status, kStNaN);
             zz = INFINITY;
         }
-        skey[q] = order_key(zz);
-        sid[q] = A.id0[gs];
-        ssrc[q] = src;
+        const uint64_t kz = order_key(zz);
+        el[q] = make_uint4((uint32_t)kz, (uint32_t)(kz >> 32), A.id0[gs], src);
     }
     __syncthreads();
     // (2) bitonic sort by (z, id); every compare ascending, i < j, j < nk
-    //     (32-bit indices; strides are powers of two, so / and % are shifts)
+    //     (32-bit indices; strides are powers of two, so / and % are shifts).
+    //     Pair p of a stage touches positions inside an aligned block of
+    //     2^(lt+1); with nw warps each warp owns the aligned chunk of 2^lwb
+    //     positions whose pairs are p in [w 2^(lwb-1), (w+1) 2^(lwb-1)), so the
+    //     stages with lt < lwb need only the warp's own synchronisation.
     const int nk32 = (int)nk;
     int lg = 0;
     while ((1 << lg) < nk32) ++lg;
-    for (int ls = 1; ls <= lg; ++ls) {          // merge size 2^ls
-        for (int lt = ls - 1; lt >= 0; --lt) {   // compare stride 2^lt
-            const int stride = 1 << lt;
-            for (int p = threadIdx.x; p < (1 << (lg - 1)); p += blockDim.x) {
-                int i, j;
-                if (lt == ls - 1) {  // first step of a merge: mirror compare
-                    int blk = p >> lt, off = p & (stride - 1);
-                    i = (blk << ls) + off;
-                    j = (blk << ls) + (1 << ls) - 1 - off;
-                } else {
-                    i = ((p >> lt) << (lt + 1)) + (p & (stride - 1));
-                    j = i + stride;
-                }
-                if (j < nk32 && zless(skey[j], sid[j], skey[i], sid[i])) {
-                    uint64_t tk = skey[i]; skey[i] = skey[j]; skey[j] = tk;
-                    uint32_t ti = sid[i]; sid[i] = sid[j]; sid[j] = ti;
-                    uint32_t ts = ssrc[i]; ssrc[i] = ssrc[j]; ssrc[j] = ts;
-                }
-            }
-            __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int lgw = 31 - __clz((int)(blockDim.x >> 5));  // blockDim a power-of-two multiple of 32
+    const int lwb = lg - lgw;
+    auto stage = [&](int ls, int lt, int p) {
+        const int stride = 1 << lt;
+        int i, j;
+        if (lt == ls - 1) {  // first step of a merge: mirror compare
+            const int blk = p >> lt, off = p & (stride - 1);
+            i = (blk << ls) + off;
+            j = (blk << ls) + (1 << ls) - 1 - off;
+        } else {
+            i = ((p >> lt) << (lt + 1)) + (p & (stride - 1));
+            j = i + stride;
         }
+        if (j < nk32) {
+            const uint4 a = el[i], b = el[j];
+            if (zless(b, a)) {
+                el[i] = b;
+                el[j] = a;
+            }
+        }
+    };
+    for (int ls = 1; ls <= lg; ++ls) {           // merge size 2^ls
+        for (int lt = ls - 1; lt >= 0; --lt) {    // compare stride 2^lt
+            if (lt >= lwb) {  // pairs span warps
+                for (int p = threadIdx.x; p < (1 << (lg - 1)); p += blockDim.x) stage(ls, lt, p);
+                __syncthreads();
+            } else {
+                const int p1 = (w + 1) << (lwb - 1);
+                for (int p = (w << (lwb - 1)) + lane; p < p1; p += 32) stage(ls, lt, p);
+                __syncwarp();
+            }
+        }
+        // a merge that ended in warp-local stages is followed by a block barrier
+        // when the next merge opens with a cross-warp stage, and at the end
+        if (lwb >= 1 && (ls >= lwb || ls == lg)) __syncthreads();
     }
     // (3) bounds: radial edges of the zone, then one thread per cell
     __shared__ double rlo_s, rhi_s;
@@ -342,20 +406,20 @@ __global__ void __launch_bounds__(1024) k_zone(ZoneArgs A)
         int64_t nc = zb + (c < zr ? 1 : 0), cs = c * zb + (c < zr ? c : zr);
         double zlo = 0.0, zhi = 0.0;
         if (nc > 0) {
-            double zf = key_value(skey[cs]), zl = key_value(skey[cs + nc - 1]);
+            double zf = key_value(el_key(el[cs])), zl = key_value(el_key(el[cs + nc - 1]));
             if (nk == 1) {
                 double H = gas_at<double>(A.params[d], rcen, 0.0).H;
                 zlo = __dsub_rn(zf, __dmul_rn(0.5, H));
                 zhi = __dadd_rn(zf, __dmul_rn(0.5, H));
             } else {
                 if (c == 0)
-                    zlo = __dsub_rn(zf, __dmul_rn(__dsub_rn(key_value(skey[1]), zf), 0.5));
+                    zlo = __dsub_rn(zf, __dmul_rn(__dsub_rn(key_value(el_key(el[1])), zf), 0.5));
                 else
-                    zlo = __dmul_rn(__dadd_rn(key_value(skey[cs - 1]), zf), 0.5);
+                    zlo = __dmul_rn(__dadd_rn(key_value(el_key(el[cs - 1])), zf), 0.5);
                 if (c + 1 < nonempty_z)
-                    zhi = __dmul_rn(__dadd_rn(zl, key_value(skey[cs + nc])), 0.5);
+                    zhi = __dmul_rn(__dadd_rn(zl, key_value(el_key(el[cs + nc]))), 0.5);
                 else
-                    zhi = __dadd_rn(zl, __dmul_rn(__dsub_rn(zl, key_value(skey[nk - 2])), 0.5));
+                    zhi = __dadd_rn(zl, __dmul_rn(__dsub_rn(zl, key_value(el_key(el[nk - 2]))), 0.5));
             }
         }
         double b0 = nc > 0 ? rlo : 0.0, b1 = nc > 0 ? rhi : 0.0;
@@ -372,13 +436,15 @@ __global__ void __launch_bounds__(1024) k_zone(ZoneArgs A)
         A.cell_n[c0 + c] = (int32_t)nc;
     }
     // (4) gather the particle columns into cell order
+#pragma unroll 4
     for (int64_t q = threadIdx.x; q < nk; q += blockDim.x) {
-        int64_t gs = D.p_off + ssrc[q], gd = D.p_off + zs + q;
+        const uint4 e = el[q];
+        int64_t gs = D.p_off + e.w, gd = D.p_off + zs + q;
         A.m1[gd] = A.m0[gs];
         A.M1[gd] = A.M0[gs];
         A.r1[gd] = A.r0[gs];
-        A.z1[gd] = key_value(skey[q]);
-        A.id1[gd] = sid[q];
+        A.z1[gd] = key_value(el_key(e));
+        A.id1[gd] = e.z;
     }
 }
 
@@ -410,6 +476,8 @@ static size_t zone_smem_bytes(const mcd_ctx *c)
 
 cudaError_t prepare_zone(mcd_ctx *c)
 {
+    cudaError_t e = cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterStage);
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_zone, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zone_smem_bytes(c));
 }
 
@@ -429,9 +497,9 @@ cudaError_t launch_regrid(mcd_ctx *c)
                                                                      c->hist);
         k_scan_blocks<<<nsb, kScanThreads, 0, st>>>(c->hist, H, c->scan_part);
         k_scan_parts<<<1, kScanThreads, 0, st>>>(c->scan_part, nsb);
-        k_radix_scatter<<<(unsigned)c->n_tiles, kRadixThreads, 0, st>>>(c->d_disks, c->tile_disk, c->key[src],
-                                                                        c->val[src], c->key[dst], c->val[dst],
-                                                                        shift, c->hist, c->scan_part);
+        k_radix_scatter<<<(unsigned)c->n_tiles, kRadixThreads, kScatterStage, st>>>(
+            c->d_disks, c->tile_disk, c->key[src], c->val[src], c->key[dst], c->val[dst], shift, c->hist,
+            c->scan_part);
     }
     // kRadixPasses is even: the sorted keys are back in buffer 0
     k_count_alive<<<(c->n_disks + 63) / 64, 64, 0, st>>>(c->d_disks, c->n_disks, c->key[0], c->n_alive, c->status);
@@ -450,7 +518,7 @@ cudaError_t launch_regrid(mcd_ctx *c)
     A.cell_V = c->cell_V;
     A.status = c->status;
     size_t sm = zone_smem_bytes(c);
-    k_zone<<<(unsigned)c->Z, 1024, sm, st>>>(A);
+    k_zone<<<(unsigned)c->Z, kZoneThreads, sm, st>>>(A);
     k_dead_tail<<<gN, 256, 0, st>>>(c->d_disks, c->slot_disk, c->N, c->n_alive, c->val[0], c->m[b], c->M[b], c->r[b],
                                     c->z[b], c->id[b], c->m[nb], c->M[nb], c->r[nb], c->z[nb], c->id[nb]);
     c->launches += 4 + 4 * kRadixPasses;
