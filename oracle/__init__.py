@@ -98,6 +98,7 @@ def lib():
         L.orc_run.argtypes = [_P(Params), C.c_int32, C.c_int32, C.c_int64, _d, _d, _d, _d, _u32, C.c_double,
                               C.c_double, C.c_int64, C.c_int64, C.c_uint64, C.c_uint64, C.c_int64, C.c_int64,
                               _d, _i64, C.c_int32]
+        L.orc_moments.argtypes = [C.c_int64, _d, _d, _d, C.c_int32, _d, _d]
         _lib = L
     return _lib
 
@@ -263,3 +264,14 @@ def run(params: dict, n_r: int, n_z: int, s: DiskState, t0: float, dt: float, st
     s.accreted += float(acc[0])
     s.events += int(ev[0])
     return st
+
+
+def moments(m, M, r, edges):
+    """Per radial bin [edges[b], edges[b+1]): (sum M, sum M m, sum M m^2,
+    sum M m^3, count) over the particles, an (nbins, 5) array."""
+    m, M, r, edges = _f64(m), _f64(M), _f64(r), _f64(edges)
+    nb = edges.size - 1
+    out = np.zeros((nb, 5))
+    lib().orc_moments(m.size, _ptr(m, C.c_double), _ptr(M, C.c_double), _ptr(r, C.c_double), nb,
+                      _ptr(edges, C.c_double), _ptr(out, C.c_double))
+    return out

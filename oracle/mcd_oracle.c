@@ -759,4 +759,40 @@ int orc_run(const orc_params *P, int32_t n_r, int32_t n_z, int64_t N, double *m,
     return status;
 }
 
+/* ---- diagnostics --------------------------------------------------------
+ * The mass distribution versus distance (the Results compare mcdust and
+ * dustpy by the dust surface density per mass and radius), summarised per
+ * radial bin: over the particles whose r lies in [edges[b], edges[b+1]) the
+ * swarm-mass-weighted sums S0 = sum M, S_k = sum M m^k (k = 1..3) and the
+ * count, each by Neumaier's compensated summation in particle order.  A
+ * particle outside [edges[0], edges[nbins]) -- a removed one has r = +inf --
+ * counts nowhere.  out: nbins x 5, (S0, S1, S2, S3, count) per bin.  The
+ * mass-weighted moments of the representative mass are S_k / S0. */
+static void orc_nsum(double *s, double *c, double x)
+{
+    double t = *s + x;
+    if (fabs(*s) >= fabs(x))
+        *c += (*s - t) + x;
+    else
+        *c += (x - t) + *s;
+    *s = t;
+}
+
+void orc_moments(int64_t N, const double *m, const double *M, const double *r, int32_t nbins, const double *edges,
+                 double *out)
+{
+    double *acc = (double *)calloc((size_t)nbins * 10, sizeof(double)); /* (sum, compensation) x 5 */
+    for (int64_t i = 0; i < N; ++i) {
+        if (!(r[i] >= edges[0] && r[i] < edges[nbins])) continue;
+        int32_t b = 0;
+        while (b + 1 < nbins && edges[b + 1] <= r[i]) ++b; /* the last edge not above r */
+        const double w = M[i], x = m[i];
+        const double v[5] = {w, w * x, w * x * x, w * x * x * x, 1.0};
+        for (int k = 0; k < 5; ++k) orc_nsum(&acc[10 * b + 2 * k], &acc[10 * b + 2 * k + 1], v[k]);
+    }
+    for (int32_t b = 0; b < nbins; ++b)
+        for (int k = 0; k < 5; ++k) out[5 * b + k] = acc[10 * b + 2 * k] + acc[10 * b + 2 * k + 1];
+    free(acc);
+}
+
 int orc_abi_version(void) { return 1; }

@@ -62,6 +62,22 @@ __global__ void k_regrid_keys(const DiskDev *disks, const int32_t *slot_disk, in
     val[dst] = (uint32_t)(s - disks[d].p_off);
 }
 
+// Lanes of the warp holding the same 8-bit digit as this lane, among the lanes
+// with ok set (an empty lane gets 0): the AND over the digit's bits of each
+// bit's ballot or its complement.  Nine independent ballots; a warp match
+// costs more once the lanes hold many distinct values.
+__device__ __forceinline__ unsigned digit_peers(int digit, bool ok)
+{
+    unsigned peers = __ballot_sync(0xffffffffu, ok);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const bool bit = (digit >> b) & 1;
+        const unsigned m = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? m : ~m;
+    }
+    return ok ? peers : 0u;
+}
+
 // histogram index of (tile t of disk d, digit b)
 __device__ __forceinline__ int64_t hidx(const DiskDev &D, int64_t t, int b)
 {
@@ -153,7 +169,7 @@ constexpr size_t kScatterStage = (size_t)kRadixTile * (sizeof(uint64_t) + sizeof
 // warps), stage the tile in shared memory in digit order, and write it out
 // run by run, so consecutive threads store consecutive addresses of a digit's
 // destination range.
-__global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const DiskDev *disks, const int32_t *tile_disk,
+__global__ void __launch_bounds__(kRadixThreads, 2) k_radix_scatter(const DiskDev *disks, const int32_t *tile_disk,
                                                                  const uint64_t *ksrc, const uint32_t *vsrc,
                                                                  uint64_t *kdst, uint32_t *vdst, int shift,
                                                                  const uint32_t *hist, const uint32_t *part)
@@ -191,10 +207,10 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const DiskDev *
     for (int it = 0; it < kRadixItems; ++it) {
         const int lq = w * (32 * kRadixItems) + it * 32 + lane;
         const bool ok = lq < nvalid;
-        int digit = ok ? (int)((kk[it] >> shift) & 255) : 256;
-        dg[it] = digit;
-        unsigned peers = __match_any_sync(0xffffffffu, digit);
-        int leader = __ffs(peers) - 1;
+        const int digit = (int)((kk[it] >> shift) & 255);
+        dg[it] = ok ? digit : 256;
+        const unsigned peers = digit_peers(digit, ok);
+        const int leader = ok ? __ffs(peers) - 1 : lane;
         uint32_t old = 0;
         if (lane == leader && ok) {
             old = wcnt[w][digit];
@@ -276,6 +292,87 @@ __device__ __forceinline__ bool zless(const uint4 &a, const uint4 &b)
 }
 
 constexpr int kZoneThreads = 512;  // two zones per SM
+constexpr int kZoneItems = 8;      // radix path: elements per lane, zones up to 16 x 32 x 8 = 4,096
+constexpr int kZoneRadixMax = (kZoneThreads / 32) * 32 * kZoneItems;
+
+// digit of element e in pass p: the first id_passes take the id's bytes, the
+// next eight the z key's (least significant first)
+__device__ __forceinline__ int zdigit(const uint4 &e, int p, int id_passes)
+{
+    return p < id_passes ? (int)((e.z >> (8 * p)) & 255u) : (int)((el_key(e) >> (8 * (p - id_passes))) & 255u);
+}
+
+// Stable LSD radix sort of a[0, n) by (z key, id): the id's bytes first, then
+// the z key's, so elements equal in z end in id order.  Each pass ranks a
+// warp's items with a warp match (item order it, lane within a warp; warps in
+// order), offsets every (warp, digit) run and scatters into the other buffer.
+// Returns the buffer that holds the result.  n <= kZoneRadixMax.
+__device__ uint4 *zone_radix(uint4 *a, uint4 *b, int n, int id_passes)
+{
+    __shared__ uint16_t wcnt[kZoneThreads / 32][kRadixBins];
+    __shared__ uint32_t doff[kRadixBins], wsum[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int per_warp = ((n + nw - 1) / nw + 31) & ~31;
+    const unsigned below = (1u << lane) - 1u;
+    for (int p = 0; p < id_passes + 8; ++p) {
+        for (int q = threadIdx.x; q < nw * kRadixBins; q += blockDim.x) (&wcnt[0][0])[q] = 0;
+        __syncthreads();
+        uint32_t dr[kZoneItems];  // digit | rank << 9
+#pragma unroll
+        for (int it = 0; it < kZoneItems; ++it) {
+            const int q = w * per_warp + it * 32 + lane;
+            const bool ok = it * 32 < per_warp && q < n;
+            const int d = ok ? zdigit(a[q], p, id_passes) : 256;
+            const unsigned peers = digit_peers(d & 255, ok);
+            const int leader = ok ? __ffs(peers) - 1 : lane;
+            uint32_t old = 0;
+            if (lane == leader && ok) {
+                old = wcnt[w][d];
+                wcnt[w][d] = (uint16_t)(old + __popc(peers));
+            }
+            old = __shfl_sync(0xffffffffu, old, leader);
+            dr[it] = (uint32_t)d | ((old + __popc(peers & below)) << 9);
+            __syncwarp();
+        }
+        __syncthreads();
+        // per digit: the warps' offsets within it, then the digits' offsets
+        if (threadIdx.x < kRadixBins) {
+            const int d = threadIdx.x;
+            uint32_t tot = 0;
+            for (int ww = 0; ww < nw; ++ww) {
+                const uint32_t c = wcnt[ww][d];
+                wcnt[ww][d] = (uint16_t)tot;
+                tot += c;
+            }
+            uint32_t v = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            if (lane == 31) wsum[w] = v;
+            doff[d] = v - tot;  // exclusive within the warp; warp offsets added below
+        }
+        __syncthreads();
+        if (threadIdx.x < kRadixBins) {
+            uint32_t o = 0;
+            for (int ww = 0; ww < w; ++ww) o += wsum[ww];
+            doff[threadIdx.x] += o;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < kZoneItems; ++it) {
+            const int q = w * per_warp + it * 32 + lane;
+            const int d = (int)(dr[it] & 511u);
+            if (d < 256) b[doff[d] + wcnt[w][d] + (dr[it] >> 9)] = a[q];
+        }
+        __syncthreads();
+        uint4 *t = a;
+        a = b;
+        b = t;
+    }
+    return a;
+}
 
 struct ZoneArgs {
     const mcd_disk_params *params;
@@ -292,6 +389,9 @@ struct ZoneArgs {
     int32_t *cell_n;
     double *cell_b, *cell_V;
     int32_t *status;
+    int64_t zcap;   // elements per buffer (the largest zone)
+    int radix;      // 1: radix sort in two buffers (zcap <= kZoneRadixMax); 0: bitonic in one
+    int id_passes;  // radix path: bytes of the largest id
 };
 
 __global__ void __launch_bounds__(kZoneThreads, 2) k_zone(ZoneArgs A)
@@ -327,51 +427,56 @@ __global__ void __launch_bounds__(kZoneThreads, 2) k_zone(ZoneArgs A)
         el[q] = make_uint4((uint32_t)kz, (uint32_t)(kz >> 32), A.id0[gs], src);
     }
     __syncthreads();
-    // (2) bitonic sort by (z, id); every compare ascending, i < j, j < nk
-    //     (32-bit indices; strides are powers of two, so / and % are shifts).
-    //     Pair p of a stage touches positions inside an aligned block of
-    //     2^(lt+1); with nw warps each warp owns the aligned chunk of 2^lwb
-    //     positions whose pairs are p in [w 2^(lwb-1), (w+1) 2^(lwb-1)), so the
-    //     stages with lt < lwb need only the warp's own synchronisation.
-    const int nk32 = (int)nk;
-    int lg = 0;
-    while ((1 << lg) < nk32) ++lg;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int lgw = 31 - __clz((int)(blockDim.x >> 5));  // blockDim a power-of-two multiple of 32
-    const int lwb = lg - lgw;
-    auto stage = [&](int ls, int lt, int p) {
-        const int stride = 1 << lt;
-        int i, j;
-        if (lt == ls - 1) {  // first step of a merge: mirror compare
-            const int blk = p >> lt, off = p & (stride - 1);
-            i = (blk << ls) + off;
-            j = (blk << ls) + (1 << ls) - 1 - off;
-        } else {
-            i = ((p >> lt) << (lt + 1)) + (p & (stride - 1));
-            j = i + stride;
-        }
-        if (j < nk32) {
-            const uint4 a = el[i], b = el[j];
-            if (zless(b, a)) {
-                el[i] = b;
-                el[j] = a;
-            }
-        }
-    };
-    for (int ls = 1; ls <= lg; ++ls) {           // merge size 2^ls
-        for (int lt = ls - 1; lt >= 0; --lt) {    // compare stride 2^lt
-            if (lt >= lwb) {  // pairs span warps
-                for (int p = threadIdx.x; p < (1 << (lg - 1)); p += blockDim.x) stage(ls, lt, p);
-                __syncthreads();
+    // (2) sort by (z, id)
+    if (A.radix) {
+        el = zone_radix(el, el + A.zcap, (int)nk, A.id_passes);
+    } else {
+        // (2) bitonic sort by (z, id); every compare ascending, i < j, j < nk
+        //     (32-bit indices; strides are powers of two, so / and % are shifts).
+        //     Pair p of a stage touches positions inside an aligned block of
+        //     2^(lt+1); with nw warps each warp owns the aligned chunk of 2^lwb
+        //     positions whose pairs are p in [w 2^(lwb-1), (w+1) 2^(lwb-1)), so the
+        //     stages with lt < lwb need only the warp's own synchronisation.
+        const int nk32 = (int)nk;
+        int lg = 0;
+        while ((1 << lg) < nk32) ++lg;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        const int lgw = 31 - __clz((int)(blockDim.x >> 5));  // blockDim a power-of-two multiple of 32
+        const int lwb = lg - lgw;
+        auto stage = [&](int ls, int lt, int p) {
+            const int stride = 1 << lt;
+            int i, j;
+            if (lt == ls - 1) {  // first step of a merge: mirror compare
+                const int blk = p >> lt, off = p & (stride - 1);
+                i = (blk << ls) + off;
+                j = (blk << ls) + (1 << ls) - 1 - off;
             } else {
-                const int p1 = (w + 1) << (lwb - 1);
-                for (int p = (w << (lwb - 1)) + lane; p < p1; p += 32) stage(ls, lt, p);
-                __syncwarp();
+                i = ((p >> lt) << (lt + 1)) + (p & (stride - 1));
+                j = i + stride;
             }
+            if (j < nk32) {
+                const uint4 a = el[i], b = el[j];
+                if (zless(b, a)) {
+                    el[i] = b;
+                    el[j] = a;
+                }
+            }
+        };
+        for (int ls = 1; ls <= lg; ++ls) {           // merge size 2^ls
+            for (int lt = ls - 1; lt >= 0; --lt) {    // compare stride 2^lt
+                if (lt >= lwb) {  // pairs span warps
+                    for (int p = threadIdx.x; p < (1 << (lg - 1)); p += blockDim.x) stage(ls, lt, p);
+                    __syncthreads();
+                } else {
+                    const int p1 = (w + 1) << (lwb - 1);
+                    for (int p = (w << (lwb - 1)) + lane; p < p1; p += 32) stage(ls, lt, p);
+                    __syncwarp();
+                }
+            }
+            // a merge that ended in warp-local stages is followed by a block barrier
+            // when the next merge opens with a cross-warp stage, and at the end
+            if (lwb >= 1 && (ls >= lwb || ls == lg)) __syncthreads();
         }
-        // a merge that ended in warp-local stages is followed by a block barrier
-        // when the next merge opens with a cross-warp stage, and at the end
-        if (lwb >= 1 && (ls >= lwb || ls == lg)) __syncthreads();
     }
     // (3) bounds: radial edges of the zone, then one thread per cell
     __shared__ double rlo_s, rhi_s;
@@ -467,18 +572,35 @@ __global__ void k_dead_tail(const DiskDev *disks, const int32_t *slot_disk, int6
     id1[s] = id0[gs];
 }
 
-static size_t zone_smem_bytes(const mcd_ctx *c)
+// the zone sort: the largest zone's size, the path (radix when the zone fits
+// its item count; both paths hold 16-byte elements, the radix path twice) and
+// the dynamic shared memory it takes
+struct ZonePlan {
+    int64_t zcap;
+    int radix, id_passes;
+    size_t smem;
+};
+static ZonePlan zone_plan(const mcd_ctx *c)
 {
-    int64_t zcap = 0;
-    for (auto &g : c->hg) zcap = zcap > (int64_t)g.n_z * g.per_cell ? zcap : (int64_t)g.n_z * g.per_cell;
-    return (size_t)zcap * 16;
+    ZonePlan z{0, 0, 0, 0};
+    int64_t n0max = 0;
+    for (size_t d = 0; d < c->hg.size(); ++d) {
+        const int64_t zc = (int64_t)c->hg[d].n_z * c->hg[d].per_cell;
+        z.zcap = z.zcap > zc ? z.zcap : zc;
+        const int64_t n0 = (int64_t)c->hg[d].n_r * zc;
+        n0max = n0max > n0 ? n0max : n0;
+    }
+    z.radix = z.zcap <= kZoneRadixMax;
+    for (int64_t idmax = n0max - 1; idmax > 0; idmax >>= 8) ++z.id_passes;
+    z.smem = (size_t)z.zcap * sizeof(uint4) * (z.radix ? 2 : 1);
+    return z;
 }
 
 cudaError_t prepare_zone(mcd_ctx *c)
 {
     cudaError_t e = cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterStage);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_zone, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zone_smem_bytes(c));
+    return cudaFuncSetAttribute(k_zone, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zone_plan(c).smem);
 }
 
 cudaError_t launch_regrid(mcd_ctx *c)
@@ -517,8 +639,11 @@ cudaError_t launch_regrid(mcd_ctx *c)
     A.cell_b = c->cell_b;
     A.cell_V = c->cell_V;
     A.status = c->status;
-    size_t sm = zone_smem_bytes(c);
-    k_zone<<<(unsigned)c->Z, kZoneThreads, sm, st>>>(A);
+    const ZonePlan zp = zone_plan(c);
+    A.zcap = zp.zcap;
+    A.radix = zp.radix;
+    A.id_passes = zp.id_passes;
+    k_zone<<<(unsigned)c->Z, kZoneThreads, zp.smem, st>>>(A);
     k_dead_tail<<<gN, 256, 0, st>>>(c->d_disks, c->slot_disk, c->N, c->n_alive, c->val[0], c->m[b], c->M[b], c->r[b],
                                     c->z[b], c->id[b], c->m[nb], c->M[nb], c->r[nb], c->z[nb], c->id[nb]);
     c->launches += 4 + 4 * kRadixPasses;

@@ -567,3 +567,45 @@ def test_regrid_matches_bruteforce(N, n_r, n_z, seed):
 def test_regrid_rejects_nan():
     s = oracle.DiskState(np.ones(3), np.ones(3), np.array([AU, np.nan, 2 * AU]), np.zeros(3), np.arange(3))
     assert oracle.regrid(P0, 1, 1, s)[0] == oracle.ENAN
+
+
+# ---- diagnostics: mass-weighted sums per radial bin --------------------------
+def _moments_brute(m, M, r, edges):
+    """Each particle's bin by a library search (numpy), each sum exactly
+    rounded (math.fsum)."""
+    import math
+    nb = len(edges) - 1
+    cols = [[[] for _ in range(5)] for _ in range(nb)]
+    b = np.searchsorted(edges, r, side="right") - 1
+    for i in range(len(r)):
+        if not (edges[0] <= r[i] < edges[-1]):
+            continue
+        w, x = M[i], m[i]
+        for k, v in enumerate((w, w * x, w * x * x, w * x * x * x, 1.0)):
+            cols[b[i]][k].append(v)
+    return np.array([[math.fsum(cols[q][k]) for k in range(5)] for q in range(nb)])
+
+
+def test_moments_match_brute_force_and_edges():
+    rng = np.random.default_rng(11)
+    n = 5000
+    edges = AU * np.geomspace(1.0, 100.0, 17)
+    r = AU * np.exp(rng.uniform(np.log(0.5), np.log(150.0), n))
+    r[:17] = edges                  # exactly on every edge (the last edge is outside)
+    r[17:20] = [np.inf, np.nan, 0.0]
+    m = W.random_masses(n, seed=3, lo=1e-11, hi=1e6)
+    M = rng.uniform(1e24, 1e27, n)
+    got = oracle.moments(m, M, r, edges)
+    want = _moments_brute(m, M, r, edges)
+    assert np.array_equal(got[:, 4], want[:, 4])
+    assert np.allclose(got, want, rtol=1e-14, atol=0.0)
+    # a particle on an interior edge belongs to the bin above it
+    one = oracle.moments([2.0], [3.0], [edges[5]], edges)
+    assert one[5, 4] == 1.0 and one[:, 4].sum() == 1.0
+    # repeated edges: the empty bin between them stays empty
+    e2 = np.array([1.0, 2.0, 2.0, 3.0])
+    two = oracle.moments([1.0, 1.0], [1.0, 1.0], [2.0, 2.5], e2)
+    assert list(two[:, 4]) == [0.0, 0.0, 2.0]
+    # moments of a single-mass bin are the mass's powers
+    mono = oracle.moments(np.full(4, 7.0), np.full(4, 2.0), np.full(4, 1.5), [1.0, 2.0])
+    assert np.allclose(mono[0, 1:4] / mono[0, 0], [7.0, 49.0, 343.0], rtol=1e-15)
