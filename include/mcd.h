@@ -198,6 +198,22 @@ int mcd_get_cell_events(mcd_ctx *ctx, int32_t disk, int64_t *events, int32_t whe
 int mcd_get_event_log(mcd_ctx *ctx, int32_t *ijo, double *t, double *m_new, int64_t cap, int64_t *n);
 
 int mcd_get_stats(mcd_ctx *ctx, int32_t disk, mcd_stats *out);
+
+/* Diagnostics (Benchmark section: the dust surface density as a function of
+ * particle mass and distance from the star, here summarised per radial bin).
+ * For every bin b = [edges[b], edges[b+1]) of disk `disk`, over the particles
+ * whose r lies in it (a removed particle has r = +inf and counts nowhere):
+ *   out[5b + 0] = sum M_i, out[5b + 1] = sum M_i m_i, out[5b + 2] = sum M_i m_i^2,
+ *   out[5b + 3] = sum M_i m_i^3, out[5b + 4] = the number of particles.
+ * The mass-weighted moments of the representative mass are out[5b+k]/out[5b].
+ * Sums are compensated (Neumaier) and combined in a fixed order, so repeated
+ * calls give the same bits.  edges: host, nbins + 1 non-decreasing values [cm]
+ * (a particle on an interior edge belongs to the bin above it); out: host,
+ * 5 * nbins doubles, filled when the call returns (it synchronises the
+ * context's stream).  1 <= nbins <= MCD_MAX_BINS; NaN or descending edges give
+ * MCD_EINVAL. */
+#define MCD_MAX_BINS 1024
+int mcd_moments(mcd_ctx *ctx, int32_t disk, int32_t nbins, const double *edges, double *out);
 int mcd_set_option(mcd_ctx *ctx, int32_t key, double value);
 
 /*

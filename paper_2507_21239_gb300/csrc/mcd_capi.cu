@@ -117,6 +117,8 @@ size_t carve(mcd_ctx *c, void *base, const Sizes &S, int32_t nd)
     x->status = cv.take<int32_t>(1);
     x->state = cv.take<StepState>(1);
     x->d_Mswarm = cv.take<double>(nd);
+    x->diag_edges = cv.take<double>(MCD_MAX_BINS + 1);
+    x->diag_out = cv.take<double>(5 * MCD_MAX_BINS);
     return (cv.off + 255) & ~(size_t)255;
 }
 
@@ -364,6 +366,21 @@ int mcd_get_particles(mcd_ctx *c, int32_t disk, double *m, double *M, double *r,
     cp(id, c->id[b] + D.p_off, 4 * D.n0);
     if (count) *count = D.n0;
     if (e == cudaSuccess && where == MCD_HOST) e = cudaStreamSynchronize(c->stream);
+    return cuda_code(e);
+}
+
+int mcd_moments(mcd_ctx *c, int32_t disk, int32_t nbins, const double *edges, double *out)
+{
+    if (!c || disk < 0 || disk >= c->n_disks || nbins <= 0 || nbins > MCD_MAX_BINS || !edges || !out)
+        return MCD_EINVAL;
+    for (int32_t b = 0; b <= nbins; ++b)
+        if (edges[b] != edges[b] || (b > 0 && edges[b] < edges[b - 1])) return MCD_EINVAL;  // NaN or descending
+    cudaError_t e = cudaMemcpyAsync(c->diag_edges, edges, sizeof(double) * (nbins + 1), cudaMemcpyHostToDevice,
+                                    c->stream);
+    if (e == cudaSuccess) e = launch_moments(c, disk, nbins);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, c->diag_out, sizeof(double) * 5 * nbins, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     return cuda_code(e);
 }
 

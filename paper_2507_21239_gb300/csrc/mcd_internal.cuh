@@ -207,6 +207,7 @@ struct mcd_ctx {
     int32_t *status = nullptr;
     mcd::StepState *state = nullptr;
     double *d_Mswarm = nullptr;  // per-disk initial swarm mass
+    double *diag_edges = nullptr, *diag_out = nullptr;  // diagnostics: bin edges, per-bin sums
     static constexpr int64_t kLogCap = 1 << 16;
 
     // options
@@ -239,6 +240,7 @@ cudaError_t launch_set_clock(mcd_ctx *c, double t, int set_t, double dt, int set
 cudaError_t launch_advance_clock(mcd_ctx *c, int add_dt_to_t);
 cudaError_t prepare_collide(mcd_ctx *c);
 cudaError_t prepare_zone(mcd_ctx *c);
+cudaError_t launch_moments(mcd_ctx *c, int disk, int nbins);
 cudaError_t launch_pair_probe(const mcd_disk_params &p, int prec, double rc, double zc, int64_t n,
                               const double *mi, const double *mj, double *dv, double *K, cudaStream_t s);
 cudaError_t launch_rate_probe(const mcd_disk_params &p, int prec, double rc, double zc, double V, int n,

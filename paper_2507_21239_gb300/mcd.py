@@ -79,6 +79,7 @@ def lib():
         L.mcd_get_cell_events.argtypes = [_vp, C.c_int32, _vp, C.c_int32]
         L.mcd_get_event_log.argtypes = [_vp, _vp, _vp, _vp, C.c_int64, _P(C.c_int64)]
         L.mcd_get_stats.argtypes = [_vp, C.c_int32, _P(mcd_stats)]
+        L.mcd_moments.argtypes = [_vp, C.c_int32, C.c_int32, _vp, _vp]
         L.mcd_set_option.argtypes = [_vp, C.c_int32, C.c_double]
         L.mcd_trace.argtypes = [_vp, C.c_int32]
         L.mcd_trace_read.argtypes = [_vp, _P(C.c_float)]
@@ -206,6 +207,18 @@ def mcd_get_stats(ctx: int, disk: int) -> mcd_stats:
     return s
 
 
+MCD_MAX_BINS = 1024
+
+
+def mcd_moments(ctx: int, disk: int, edges) -> np.ndarray:
+    """Per radial bin [edges[b], edges[b+1]) of the disk: (sum M, sum M m,
+    sum M m^2, sum M m^3, count), an (nbins, 5) array (see include/mcd.h)."""
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    out = np.zeros((e.size - 1, 5))
+    _check(lib().mcd_moments(ctx, disk, e.size - 1, e.ctypes.data, out.ctypes.data), "mcd_moments")
+    return out
+
+
 def mcd_set_option(ctx: int, key: int, value: float):
     _check(lib().mcd_set_option(ctx, key, float(value)), "mcd_set_option")
 
@@ -288,6 +301,9 @@ class Disk:
 
     def stats(self, disk: int = 0) -> mcd_stats:
         return mcd_get_stats(self.ctx, disk)
+
+    def moments(self, edges, disk: int = 0) -> np.ndarray:
+        return mcd_moments(self.ctx, disk, edges)
 
     def close(self):
         if self.ctx:

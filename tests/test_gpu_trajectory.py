@@ -1,0 +1,138 @@
+"""Statistical parity of the mixed-precision path with the oracle over whole
+disk evolutions.
+
+The mixed path evaluates rates in FP32, so its event sequence departs from the
+oracle's after the first rounding-sensitive choice; what must agree is the
+outcome in distribution.  On the 16 x 4 x 100 Benchmark-table disk, 16 seeds
+evolve for 2,000 yr (through the growth and fragmentation phases) on the GPU
+(one batched context, disk d keyed by (seed, d) like the oracle's runs) and in
+the oracle.  Per logarithmic radial bin (16 bins over r_in .. r_out):
+
+* the across-seed mean of each swarm-mass-weighted moment of the
+  representative mass (k = 1..3) and of the bin's mass agrees within
+  max(2 %, 4 sigma_seed), sigma_seed the standard error of the difference of
+  the two means (4 sigma because 64 comparisons are made);
+* a two-sample KS test on the pooled log m of the bin keeps p above 0.01 /
+  (number of bins tested) (Bonferroni);
+* every disk's mass is conserved: alive swarm mass plus accreted mass equals
+  the initial swarm mass to 1e-12.
+"""
+import multiprocessing as mp
+import os
+from concurrent.futures import ProcessPoolExecutor
+
+import numpy as np
+import pytest
+import torch
+from scipy import stats
+
+import oracle
+import oracle_runs
+from paper_2507_21239_gb300 import mcd, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+AU, YR = W.AU, W.YR
+SEEDS = 16
+DT, STEPS = 50 * YR, 40
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+class _Orc:
+    """An oracle run's particle columns (the shape the tests below read)."""
+
+    def __init__(self, m, M, r):
+        self.m, self.M, self.r = m, M, r
+
+
+def _runs():
+    wl = W.WORKLOADS["disk2d_16x4x100"]
+    P, grid = wl["params"], (wl["n_r"], wl["n_z"], wl["per_cell"])
+    edges = P["r_in"] * np.geomspace(1.0, P["r_out"] / P["r_in"], 17)
+    oracle.lib()  # built before the workers load it
+    # the oracle runs in spawned single-threaded workers while the GPU runs
+    workers = max(1, min(SEEDS, os.cpu_count() or 1))
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        futs = [ex.submit(oracle_runs.evolve, P, grid, 7, k, DT, STEPS, edges) for k in range(SEEDS)]
+        d = mcd.Disk([P] * SEEDS, [grid] * SEEDS, seed=7, prec=mcd.MCD_MIXED)
+        m0 = [d.particles(k)["M"].sum() for k in range(SEEDS)]
+        for _ in range(STEPS):
+            d.step(DT)
+        assert mcd.mcd_sync(d.ctx) == mcd.MCD_OK
+        gpu = [(d.particles(k), d.moments(edges, k), d.stats(k).accreted_mass, m0[k]) for k in range(SEEDS)]
+        d.close()
+        orc = []
+        for f in futs:
+            st, m, M, r, mom, acc, M0 = f.result()
+            assert st == 0
+            orc.append((_Orc(m, M, r), mom, acc, M0))
+    return edges, gpu, orc
+
+
+@pytest.fixture(scope="module")
+def runs():
+    return _runs()
+
+
+def test_mass_conserved(runs):
+    _, gpu, orc = runs
+    for x, mom, acc, M0 in gpu:
+        alive = np.isfinite(x["r"])
+        assert abs(x["M"][alive].sum() + acc - M0) <= 1e-12 * M0
+        assert abs(mom[:, 0].sum() - x["M"][alive].sum()) <= 1e-12 * M0
+    for s, mom, acc, M0 in orc:
+        assert abs(s.M[np.isfinite(s.r)].sum() + acc - M0) <= 1e-12 * M0
+
+
+def test_moments_agree_in_distribution(runs):
+    _, gpu, orc = runs
+
+    def table(rs):
+        S = np.array([mom for _, mom, _, _ in rs])  # seeds x bins x 5
+        mass = S[:, :, 0]
+        with np.errstate(invalid="ignore", divide="ignore"):
+            mk = S[:, :, 1:4] / mass[:, :, None]
+        return mass, mk, S[:, :, 4]
+
+    mg, kg, ng = table(gpu)
+    mo, ko, no = table(orc)
+    checked = 0
+    for b in range(mg.shape[1]):
+        # bins that hold particles in every run of both sides
+        if not (np.all(ng[:, b] > 0) and np.all(no[:, b] > 0)):
+            continue
+        cols = [(mg[:, b], mo[:, b])] + [(kg[:, b, q], ko[:, b, q]) for q in range(3)]
+        for q, (a, o) in enumerate(cols):
+            diff = abs(a.mean() - o.mean())
+            sig = np.sqrt(a.var(ddof=1) / a.size + o.var(ddof=1) / o.size)
+            assert diff <= max(0.02 * abs(o.mean()), 4.0 * sig), (b, q, a.mean(), o.mean(), sig)
+            checked += 1
+    assert checked >= 16  # most of the inner disk holds particles throughout
+
+
+def test_log_mass_ks_per_bin(runs):
+    edges, gpu, orc = runs
+    nb = edges.size - 1
+
+    def pooled(rs, getter):
+        out = [[] for _ in range(nb)]
+        for run in rs:
+            m, r = getter(run)
+            ok = np.isfinite(r) & (r >= edges[0]) & (r < edges[-1])
+            b = np.searchsorted(edges, r[ok], side="right") - 1
+            for q in range(nb):
+                out[q].append(np.log10(m[ok][b == q]))
+        return [np.concatenate(v) for v in out]
+
+    g = pooled(gpu, lambda run: (run[0]["m"], run[0]["r"]))
+    o = pooled(orc, lambda run: (run[0].m, run[0].r))
+    tested = [q for q in range(nb) if g[q].size >= 50 and o[q].size >= 50]
+    assert len(tested) >= 8
+    for q in tested:
+        p = stats.ks_2samp(g[q], o[q]).pvalue
+        assert p > 0.01 / len(tested), (q, p, g[q].size, o[q].size)
