@@ -306,11 +306,16 @@ __device__ __forceinline__ int zdigit(const uint4 &e, int p, int id_passes)
 // the z key's, so elements equal in z end in id order.  Each pass ranks a
 // warp's items with a warp match (item order it, lane within a warp; warps in
 // order), offsets every (warp, digit) run and scatters into the other buffer.
-// Returns the buffer that holds the result.  n <= kZoneRadixMax.
-__device__ uint4 *zone_radix(uint4 *a, uint4 *b, int n, int id_passes)
+// Returns the buffer that holds the result.  n <= kZoneRadixMax.  The
+// counters live in the radix path's own part of the dynamic shared memory
+// (kZoneRadixScratch bytes after the two buffers), so the bitonic path keeps
+// the whole allocation for its one buffer.
+constexpr size_t kZoneRadixScratch = sizeof(uint16_t) * (kZoneThreads / 32) * kRadixBins + sizeof(uint32_t) * (kRadixBins + 8);
+__device__ uint4 *zone_radix(uint4 *a, uint4 *b, int n, int id_passes, unsigned char *scratch)
 {
-    __shared__ uint16_t wcnt[kZoneThreads / 32][kRadixBins];
-    __shared__ uint32_t doff[kRadixBins], wsum[8];
+    uint16_t(*wcnt)[kRadixBins] = reinterpret_cast<uint16_t(*)[kRadixBins]>(scratch);
+    uint32_t *doff = reinterpret_cast<uint32_t *>(scratch + sizeof(uint16_t) * (kZoneThreads / 32) * kRadixBins);
+    uint32_t *wsum = doff + kRadixBins;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int per_warp = ((n + nw - 1) / nw + 31) & ~31;
     const unsigned below = (1u << lane) - 1u;
@@ -429,7 +434,7 @@ __global__ void __launch_bounds__(kZoneThreads, 2) k_zone(ZoneArgs A)
     __syncthreads();
     // (2) sort by (z, id)
     if (A.radix) {
-        el = zone_radix(el, el + A.zcap, (int)nk, A.id_passes);
+        el = zone_radix(el, el + A.zcap, (int)nk, A.id_passes, reinterpret_cast<unsigned char *>(el + 2 * A.zcap));
     } else {
         // (2) bitonic sort by (z, id); every compare ascending, i < j, j < nk
         //     (32-bit indices; strides are powers of two, so / and % are shifts).
@@ -592,7 +597,7 @@ static ZonePlan zone_plan(const mcd_ctx *c)
     }
     z.radix = z.zcap <= kZoneRadixMax;
     for (int64_t idmax = n0max - 1; idmax > 0; idmax >>= 8) ++z.id_passes;
-    z.smem = (size_t)z.zcap * sizeof(uint4) * (z.radix ? 2 : 1);
+    z.smem = (size_t)z.zcap * sizeof(uint4) * (z.radix ? 2 : 1) + (z.radix ? kZoneRadixScratch : 0);
     return z;
 }
 
