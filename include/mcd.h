@@ -173,6 +173,11 @@ int mcd_get_particles(mcd_ctx *ctx, int32_t disk, double *m, double *M, double *
  * Replace disk `disk`'s particles (count must equal its initial particle
  * count; ids a permutation of 0..count-1; r = +inf marks a removed particle).
  * Cells become stale: call mcd_regrid before mcd_collide.
+ * The columns are staged on the device and the ids checked there; only a
+ * permutation replaces the live state, which bad ids leave untouched.
+ * where = MCD_HOST: host arrays, synchronises, returns MCD_EINVAL for bad ids.
+ * where = MCD_DEVICE: device arrays, asynchronous; bad ids latch MCD_EINVAL
+ * in the status word (mcd_sync / mcd_get_stats).
  */
 int mcd_set_particles(mcd_ctx *ctx, int32_t disk, const double *m, const double *M, const double *r,
                       const double *z, const uint32_t *id, int64_t count, int32_t where);

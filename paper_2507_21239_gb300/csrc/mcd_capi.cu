@@ -384,33 +384,93 @@ int mcd_moments(mcd_ctx *c, int32_t disk, int32_t nbins, const double *edges, do
     return cuda_code(e);
 }
 
+namespace {
+
+// Staged replacement of one disk's particles: the new columns sit in the
+// disk's range of the inactive state buffer (free between steps), the ids are
+// counted there (each must occur exactly once and be below n0), and only a
+// clean count lets the columns into the live buffer.
+__global__ void k_ids_count(const uint32_t *id, int64_t n, uint32_t *cnt, int32_t *bad)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const uint32_t v = id[k];
+    if ((int64_t)v >= n)
+        atomicOr(bad, 1);
+    else
+        atomicAdd(&cnt[v], 1u);
+}
+
+__global__ void k_ids_verify(const uint32_t *cnt, int64_t n, int32_t *bad)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < n && cnt[k] != 1u) atomicOr(bad, 1);
+}
+
+__global__ void k_ids_commit(const int32_t *bad, int64_t n, const double *m, const double *M, const double *r,
+                             const double *z, const uint32_t *id, double *m1, double *M1, double *r1, double *z1,
+                             uint32_t *id1, int32_t *status)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (*bad) {
+        if (k == 0 && status) atomicOr(status, kStBadCell);
+        return;
+    }
+    if (k >= n) return;
+    m1[k] = m[k];
+    M1[k] = M[k];
+    r1[k] = r[k];
+    z1[k] = z[k];
+    id1[k] = id[k];
+}
+
+}  // namespace
+
 int mcd_set_particles(mcd_ctx *c, int32_t disk, const double *m, const double *M, const double *r, const double *z,
                       const uint32_t *id, int64_t count, int32_t where)
 {
     if (!c || disk < 0 || disk >= c->n_disks || (where != MCD_HOST && where != MCD_DEVICE)) return MCD_EINVAL;
     const DiskDev &D = c->hd[disk];
     if (count != D.n0 || !m || !M || !r || !z || !id) return MCD_EINVAL;
-    if (where == MCD_HOST) {
-        std::vector<char> seen(D.n0, 0);
-        for (int64_t k = 0; k < D.n0; ++k) {
-            if ((int64_t)id[k] >= D.n0 || seen[id[k]]) return MCD_EINVAL;
-            seen[id[k]] = 1;
-        }
-    }
-    const int b = c->cur;
+    const int b = c->cur, sb = 1 - c->cur;  // live buffer, staging buffer
+    const int64_t o = D.p_off, n = D.n0;
     cudaMemcpyKind kind = where == MCD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     cudaError_t e = cudaSuccess;
-    auto cp = [&](void *dst, const void *src, size_t n) {
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, n, kind, c->stream);
+    auto cp = [&](void *dst, const void *src, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, kind, c->stream);
     };
-    cp(c->m[b] + D.p_off, m, 8 * D.n0);
-    cp(c->M[b] + D.p_off, M, 8 * D.n0);
-    cp(c->r[b] + D.p_off, r, 8 * D.n0);
-    cp(c->z[b] + D.p_off, z, 8 * D.n0);
-    cp(c->id[b] + D.p_off, id, 4 * D.n0);
-    if (e == cudaSuccess && where == MCD_HOST) e = cudaStreamSynchronize(c->stream);
+    cp(c->m[sb] + o, m, 8 * n);
+    cp(c->M[sb] + o, M, 8 * n);
+    cp(c->r[sb] + o, r, 8 * n);
+    cp(c->z[sb] + o, z, 8 * n);
+    cp(c->id[sb] + o, id, 4 * n);
+    // the id counts go to the sort's value buffer, the verdict to its histogram
+    // (both free between regrids)
+    uint32_t *cnt = c->val[1] + o;
+    int32_t *bad = reinterpret_cast<int32_t *>(c->hist);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, 4 * n, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, 4, c->stream);
+    const unsigned g = (unsigned)((n + 255) / 256);
+    if (e == cudaSuccess && n > 0) {
+        k_ids_count<<<g, 256, 0, c->stream>>>(c->id[sb] + o, n, cnt, bad);
+        k_ids_verify<<<g, 256, 0, c->stream>>>(cnt, n, bad);
+        k_ids_commit<<<g, 256, 0, c->stream>>>(bad, n, c->m[sb] + o, c->M[sb] + o, c->r[sb] + o, c->z[sb] + o,
+                                               c->id[sb] + o, c->m[b] + o, c->M[b] + o, c->r[b] + o, c->z[b] + o,
+                                               c->id[b] + o, where == MCD_DEVICE ? c->status : nullptr);
+        c->launches += 3;
+        e = cudaGetLastError();
+    }
     c->cells_valid = false;
-    return cuda_code(e);
+    if (e != cudaSuccess) return MCD_ECUDA;
+    if (where == MCD_HOST) {
+        // host arrays: the caller may reuse them on return, and learns of bad ids now
+        int32_t hb = 0;
+        e = cudaMemcpyAsync(&hb, bad, 4, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return MCD_ECUDA;
+        if (hb) return MCD_EINVAL;  // the live state is untouched
+    }
+    return MCD_OK;
 }
 
 int mcd_get_cells(mcd_ctx *c, int32_t disk, int64_t *cell_off, double *bounds, double *V, int32_t where)

@@ -320,9 +320,42 @@ def test_out_of_order_and_bad_ids_rejected():
         mcd.mcd_collide(d.ctx, 10 * YR)
     assert e.value.code == mcd.MCD_ESTATE
     p = d.particles()
+    before = d.particles()
     p["id"][0] = p["id"][1]
     with pytest.raises(mcd.McdError):
         mcd.mcd_set_particles(d.ctx, 0, p["m"], p["M"], p["r"], p["z"], p["id"])
+    after = d.particles()
+    for key in before:  # a rejected replacement leaves the live state as it was
+        assert np.array_equal(before[key], after[key]), key
+    assert mcd.mcd_sync(d.ctx) == mcd.MCD_OK
+    d.close()
+
+
+def test_set_particles_from_device_checks_ids():
+    """Device arrays: bad ids (a repeat, one out of range) latch MCD_EINVAL and
+    leave the state as it was; a permutation replaces it."""
+    P = W.benchmark_disk()
+    d = _make_ctx(P, (2, 2, 4))
+    before = d.particles()
+    n = before["id"].size
+    cols = {k: dev(before[k]) for k in ("m", "M", "r", "z")}
+    for bad in (np.r_[before["id"][1], before["id"][1:]], np.r_[n + 3, before["id"][1:]]):
+        idd = torch.tensor(bad.astype(np.int64), dtype=torch.int32, device="cuda")
+        mcd.mcd_set_particles(d.ctx, 0, cols["m"], cols["M"], cols["r"], cols["z"], idd, mcd.MCD_DEVICE)
+        assert mcd.mcd_sync(d.ctx) == mcd.MCD_EINVAL
+        after = d.particles()
+        for key in before:
+            assert np.array_equal(before[key], after[key]), key
+        d.close()
+        d = _make_ctx(P, (2, 2, 4))
+        before = d.particles()
+    perm = np.random.default_rng(0).permutation(n).astype(np.int32)
+    new_m = before["m"] * 2.0
+    mcd.mcd_set_particles(d.ctx, 0, dev(new_m), cols["M"], cols["r"], cols["z"],
+                          torch.tensor(perm, device="cuda"), mcd.MCD_DEVICE)
+    assert mcd.mcd_sync(d.ctx) == mcd.MCD_OK
+    got = d.particles()
+    assert np.array_equal(got["m"], new_m) and np.array_equal(got["id"], perm.astype(np.uint32))
     d.close()
 
 
