@@ -99,6 +99,7 @@ def lib():
                               C.c_double, C.c_int64, C.c_int64, C.c_uint64, C.c_uint64, C.c_int64, C.c_int64,
                               _d, _i64, C.c_int32]
         L.orc_moments.argtypes = [C.c_int64, _d, _d, _d, C.c_int32, _d, _d]
+        L.orc_sigma_map.argtypes = [C.c_int64, _d, _d, _d, C.c_int32, _d, C.c_int32, _d, _d]
         _lib = L
     return _lib
 
@@ -274,4 +275,14 @@ def moments(m, M, r, edges):
     out = np.zeros((nb, 5))
     lib().orc_moments(m.size, _ptr(m, C.c_double), _ptr(M, C.c_double), _ptr(r, C.c_double), nb,
                       _ptr(edges, C.c_double), _ptr(out, C.c_double))
+    return out
+
+
+def sigma_map(m, M, r, r_edges, m_edges):
+    """Swarm mass per (radial bin, mass bin), an (nr, nm) array."""
+    m, M, r = _f64(m), _f64(M), _f64(r)
+    re, me = _f64(r_edges), _f64(m_edges)
+    out = np.zeros((re.size - 1, me.size - 1))
+    lib().orc_sigma_map(m.size, _ptr(m, C.c_double), _ptr(M, C.c_double), _ptr(r, C.c_double), re.size - 1,
+                        _ptr(re, C.c_double), me.size - 1, _ptr(me, C.c_double), _ptr(out, C.c_double))
     return out

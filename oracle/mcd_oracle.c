@@ -795,4 +795,27 @@ void orc_moments(int64_t N, const double *m, const double *M, const double *r, i
     free(acc);
 }
 
+/* The map itself (Benchmark section: the dust surface density as a function
+ * of particle mass and distance from the star): per (radial bin b, mass bin q)
+ * the swarm mass sum M over the particles with r in [r_edges[b], r_edges[b+1])
+ * and m in [m_edges[q], m_edges[q+1]), by compensated summation in particle
+ * order.  out: nr x nm, radial bin major.  sigma_d per logarithmic mass
+ * interval is out / (pi (r_hi^2 - r_lo^2) ln(m_hi / m_lo)). */
+void orc_sigma_map(int64_t N, const double *m, const double *M, const double *r, int32_t nr, const double *r_edges,
+                   int32_t nm, const double *m_edges, double *out)
+{
+    double *acc = (double *)calloc((size_t)nr * nm * 2, sizeof(double));
+    for (int64_t i = 0; i < N; ++i) {
+        if (!(r[i] >= r_edges[0] && r[i] < r_edges[nr])) continue;
+        if (!(m[i] >= m_edges[0] && m[i] < m_edges[nm])) continue;
+        int32_t b = 0, q = 0;
+        while (b + 1 < nr && r_edges[b + 1] <= r[i]) ++b;
+        while (q + 1 < nm && m_edges[q + 1] <= m[i]) ++q;
+        const int64_t k = (int64_t)b * nm + q;
+        orc_nsum(&acc[2 * k], &acc[2 * k + 1], M[i]);
+    }
+    for (int64_t k = 0; k < (int64_t)nr * nm; ++k) out[k] = acc[2 * k] + acc[2 * k + 1];
+    free(acc);
+}
+
 int orc_abi_version(void) { return 1; }

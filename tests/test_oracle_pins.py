@@ -609,3 +609,35 @@ def test_moments_match_brute_force_and_edges():
     # moments of a single-mass bin are the mass's powers
     mono = oracle.moments(np.full(4, 7.0), np.full(4, 2.0), np.full(4, 1.5), [1.0, 2.0])
     assert np.allclose(mono[0, 1:4] / mono[0, 0], [7.0, 49.0, 343.0], rtol=1e-15)
+
+
+def test_sigma_map_matches_brute_force():
+    """Swarm mass per (radial bin, mass bin) against a library search with
+    exactly rounded sums; edge values belong to the bin above; particles
+    outside either range, removed ones and NaN masses count nowhere."""
+    import math
+    rng = np.random.default_rng(12)
+    n = 4000
+    r_edges = AU * np.geomspace(1.0, 100.0, 9)
+    m_edges = np.geomspace(1e-12, 1e4, 17)
+    r = AU * np.exp(rng.uniform(np.log(0.8), np.log(120.0), n))
+    m = np.exp(rng.uniform(np.log(1e-13), np.log(1e5), n))
+    r[:9] = r_edges
+    m[9:26] = m_edges
+    r[26], m[27], r[28] = np.inf, np.nan, np.nan
+    M = rng.uniform(1e24, 1e27, n)
+    got = oracle.sigma_map(m, M, r, r_edges, m_edges)
+    want = np.zeros_like(got)
+    cols = {}
+    b = np.searchsorted(r_edges, r, side="right") - 1
+    q = np.searchsorted(m_edges, m, side="right") - 1
+    for i in range(n):
+        if r_edges[0] <= r[i] < r_edges[-1] and m_edges[0] <= m[i] < m_edges[-1]:
+            cols.setdefault((b[i], q[i]), []).append(M[i])
+    for (bb, qq), v in cols.items():
+        want[bb, qq] = math.fsum(v)
+    assert np.allclose(got, want, rtol=1e-14, atol=0.0)
+    assert np.array_equal(got == 0, want == 0)
+    # every particle inside both ranges is counted once
+    inside = (r >= r_edges[0]) & (r < r_edges[-1]) & (m >= m_edges[0]) & (m < m_edges[-1])
+    assert math.isclose(got.sum(), math.fsum(M[inside]), rel_tol=1e-13)
