@@ -219,6 +219,22 @@ int mcd_get_stats(mcd_ctx *ctx, int32_t disk, mcd_stats *out);
  * MCD_EINVAL. */
 #define MCD_MAX_BINS 1024
 int mcd_moments(mcd_ctx *ctx, int32_t disk, int32_t nbins, const double *edges, double *out);
+
+/* The sigma_d(m, r) map (Benchmark section: the dust surface density as a
+ * function of particle mass and distance from the star): out[b * nm + q] =
+ * the swarm mass sum M_i [g] over disk `disk`'s particles with r in
+ * [r_edges[b], r_edges[b+1]) and m in [m_edges[q], m_edges[q+1]).  Divided by
+ * pi (r_hi^2 - r_lo^2) and ln(m_hi / m_lo) it is sigma_d per logarithmic mass
+ * interval.  Each M_i enters rounded to a power-of-two unit of at most 2^-61 of
+ * the disk's live swarm mass and the sums are integer, so repeated calls give
+ * the same bits.  Edges: host, non-decreasing, no NaN (MCD_EINVAL otherwise);
+ * out: host, nr * nm doubles, filled when the call returns (it synchronises
+ * the context's stream).  nr, nm <= MCD_MAX_MAP_EDGES, nr * nm <=
+ * MCD_MAX_MAP_BINS. */
+#define MCD_MAX_MAP_EDGES 4096
+#define MCD_MAX_MAP_BINS 65536
+int mcd_sigma_map(mcd_ctx *ctx, int32_t disk, int32_t nr, const double *r_edges, int32_t nm, const double *m_edges,
+                  double *out);
 int mcd_set_option(mcd_ctx *ctx, int32_t key, double value);
 
 /*

@@ -119,6 +119,10 @@ size_t carve(mcd_ctx *c, void *base, const Sizes &S, int32_t nd)
     x->d_Mswarm = cv.take<double>(nd);
     x->diag_edges = cv.take<double>(MCD_MAX_BINS + 1);
     x->diag_out = cv.take<double>(5 * MCD_MAX_BINS);
+    x->map_acc = cv.take<unsigned long long>(MCD_MAX_MAP_BINS + 1);
+    x->map_redges = cv.take<double>(MCD_MAX_MAP_EDGES + 1);
+    x->map_medges = cv.take<double>(MCD_MAX_MAP_EDGES + 1);
+    x->map_out = cv.take<double>(MCD_MAX_MAP_BINS);
     return (cv.off + 255) & ~(size_t)255;
 }
 
@@ -380,6 +384,27 @@ int mcd_moments(mcd_ctx *c, int32_t disk, int32_t nbins, const double *edges, do
     if (e == cudaSuccess) e = launch_moments(c, disk, nbins);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out, c->diag_out, sizeof(double) * 5 * nbins, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return cuda_code(e);
+}
+
+int mcd_sigma_map(mcd_ctx *c, int32_t disk, int32_t nr, const double *r_edges, int32_t nm, const double *m_edges,
+                  double *out)
+{
+    if (!c || disk < 0 || disk >= c->n_disks || nr <= 0 || nm <= 0 || nr > MCD_MAX_MAP_EDGES ||
+        nm > MCD_MAX_MAP_EDGES || (int64_t)nr * nm > MCD_MAX_MAP_BINS || !r_edges || !m_edges || !out)
+        return MCD_EINVAL;
+    for (int32_t b = 0; b <= nr; ++b)
+        if (r_edges[b] != r_edges[b] || (b > 0 && r_edges[b] < r_edges[b - 1])) return MCD_EINVAL;
+    for (int32_t q = 0; q <= nm; ++q)
+        if (m_edges[q] != m_edges[q] || (q > 0 && m_edges[q] < m_edges[q - 1])) return MCD_EINVAL;
+    cudaError_t e = cudaMemcpyAsync(c->map_redges, r_edges, sizeof(double) * (nr + 1), cudaMemcpyHostToDevice,
+                                    c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->map_medges, m_edges, sizeof(double) * (nm + 1), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_sigma_map(c, disk, nr, nm);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, c->map_out, sizeof(double) * nr * nm, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     return cuda_code(e);
 }

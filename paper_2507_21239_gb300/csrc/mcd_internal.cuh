@@ -208,6 +208,8 @@ struct mcd_ctx {
     mcd::StepState *state = nullptr;
     double *d_Mswarm = nullptr;  // per-disk initial swarm mass
     double *diag_edges = nullptr, *diag_out = nullptr;  // diagnostics: bin edges, per-bin sums
+    unsigned long long *map_acc = nullptr;  // sigma map: per-bin unit counts, then the unit's exponent
+    double *map_redges = nullptr, *map_medges = nullptr, *map_out = nullptr;
     static constexpr int64_t kLogCap = 1 << 16;
 
     // options
@@ -241,6 +243,7 @@ cudaError_t launch_advance_clock(mcd_ctx *c, int add_dt_to_t);
 cudaError_t prepare_collide(mcd_ctx *c);
 cudaError_t prepare_zone(mcd_ctx *c);
 cudaError_t launch_moments(mcd_ctx *c, int disk, int nbins);
+cudaError_t launch_sigma_map(mcd_ctx *c, int disk, int nr, int nm);
 cudaError_t launch_pair_probe(const mcd_disk_params &p, int prec, double rc, double zc, int64_t n,
                               const double *mi, const double *mj, double *dv, double *K, cudaStream_t s);
 cudaError_t launch_rate_probe(const mcd_disk_params &p, int prec, double rc, double zc, double V, int n,

@@ -80,6 +80,7 @@ def lib():
         L.mcd_get_event_log.argtypes = [_vp, _vp, _vp, _vp, C.c_int64, _P(C.c_int64)]
         L.mcd_get_stats.argtypes = [_vp, C.c_int32, _P(mcd_stats)]
         L.mcd_moments.argtypes = [_vp, C.c_int32, C.c_int32, _vp, _vp]
+        L.mcd_sigma_map.argtypes = [_vp, C.c_int32, C.c_int32, _vp, C.c_int32, _vp, _vp]
         L.mcd_set_option.argtypes = [_vp, C.c_int32, C.c_double]
         L.mcd_trace.argtypes = [_vp, C.c_int32]
         L.mcd_trace_read.argtypes = [_vp, _P(C.c_float)]
@@ -219,6 +220,17 @@ def mcd_moments(ctx: int, disk: int, edges) -> np.ndarray:
     return out
 
 
+def mcd_sigma_map(ctx: int, disk: int, r_edges, m_edges) -> np.ndarray:
+    """Swarm mass per (radial bin, mass bin) of the disk, an (nr, nm) array
+    (see include/mcd.h)."""
+    re = np.ascontiguousarray(r_edges, dtype=np.float64)
+    me = np.ascontiguousarray(m_edges, dtype=np.float64)
+    out = np.zeros((re.size - 1, me.size - 1))
+    _check(lib().mcd_sigma_map(ctx, disk, re.size - 1, re.ctypes.data, me.size - 1, me.ctypes.data,
+                               out.ctypes.data), "mcd_sigma_map")
+    return out
+
+
 def mcd_set_option(ctx: int, key: int, value: float):
     _check(lib().mcd_set_option(ctx, key, float(value)), "mcd_set_option")
 
@@ -304,6 +316,9 @@ class Disk:
 
     def moments(self, edges, disk: int = 0) -> np.ndarray:
         return mcd_moments(self.ctx, disk, edges)
+
+    def sigma_map(self, r_edges, m_edges, disk: int = 0) -> np.ndarray:
+        return mcd_sigma_map(self.ctx, disk, r_edges, m_edges)
 
     def close(self):
         if self.ctx:

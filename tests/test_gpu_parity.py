@@ -502,3 +502,29 @@ def test_moments_match_oracle(prec):
     with pytest.raises(mcd.McdError):
         d.moments(np.array([AU, np.nan, 2 * AU]))
     d.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_sigma_map_matches_oracle(prec):
+    """The sigma_d(m, r) map on the device equals the oracle's on the particles
+    the GPU holds (each M rounded to 2^-61 of the disk's mass at most; empty
+    bins exactly zero); repeated calls give the same bits; bad edges rejected."""
+    P = W.benchmark_disk(dust_to_gas=0.1)
+    d = _make_ctx(P, (8, 4, 50), seed=5, prec=prec)
+    for _ in range(3):
+        d.step(10 * YR)
+    x = d.particles()
+    r_edges = AU * np.geomspace(1.0, 100.0, 25)
+    m_edges = np.geomspace(1e-12, 1e6, 37)
+    got = d.sigma_map(r_edges, m_edges)
+    want = oracle.sigma_map(x["m"], x["M"], x["r"], r_edges, m_edges)
+    assert np.array_equal(got == 0, want == 0)
+    assert np.allclose(got, want, rtol=1e-12, atol=0.0)
+    assert np.array_equal(d.sigma_map(r_edges, m_edges), got)
+    alive = np.isfinite(x["r"])
+    assert np.isclose(got.sum(), x["M"][alive].sum(), rtol=1e-12)
+    with pytest.raises(mcd.McdError):
+        d.sigma_map(r_edges[::-1], m_edges)
+    with pytest.raises(mcd.McdError):
+        d.sigma_map(r_edges, np.geomspace(1e-12, 1e6, 5000))
+    d.close()
