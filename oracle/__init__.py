@@ -46,14 +46,16 @@ class Params(C.Structure):
         "sigma0", "p", "T0", "q", "alpha", "v_frag", "erosion_ratio",
         "dust_to_gas", "r_in", "r_out", "m_star", "rho_s", "a_mono",
         "mu", "sigma_h2", "dm_group", "frag_xi", "erosion_chi",
-        "K_const", "V_const", "m_init", "M_total")] + [
+        "K_const", "V_const", "m_init", "M_total", "frag_ramp")] + [
         (n, C.c_int32) for n in ("kernel_mode", "settle_form", "dv_flags", "tr_flags")]
+
+    OPTIONAL = {"frag_ramp": 0.0}  # keys a caller's dict may leave out
 
     @classmethod
     def from_dict(cls, d: dict) -> "Params":
         p = cls()
         for name, _ in cls._fields_:
-            setattr(p, name, d[name])
+            setattr(p, name, d[name] if name in d or name not in cls.OPTIONAL else cls.OPTIONAL[name])
         return p
 
 
@@ -82,6 +84,9 @@ def lib():
         L.orc_rate_matrix.argtypes = [_P(Params), C.c_double, C.c_double, C.c_double, C.c_int64, _d, _d, _d, _d]
         L.orc_fragment_probe.argtypes = [_P(Params), C.c_double, C.c_double, C.c_double]
         L.orc_fragment_probe.restype = C.c_double
+        L.orc_outcome_probe.argtypes = [_P(Params), C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                        _P(C.c_int32)]
+        L.orc_outcome_probe.restype = C.c_double
         L.orc_disk_dust_mass.argtypes = [_P(Params)]
         L.orc_disk_dust_mass.restype = C.c_double
         L.orc_collide_cell.argtypes = [_P(Params), C.c_double, C.c_double, C.c_double, C.c_int64, _d, _d,
@@ -286,3 +291,11 @@ def sigma_map(m, M, r, r_edges, m_edges):
     lib().orc_sigma_map(m.size, _ptr(m, C.c_double), _ptr(M, C.c_double), _ptr(r, C.c_double), re.size - 1,
                         _ptr(re, C.c_double), me.size - 1, _ptr(me, C.c_double), _ptr(out, C.c_double))
     return out
+
+
+def outcome(params: dict, mi: float, mj: float, dv: float, m0: float, u: float):
+    """(new mass of i, kind) for one event: 0 stick, 1 fragment, 2 erode."""
+    k = C.c_int32(0)
+    P = Params.from_dict(params)
+    mn = lib().orc_outcome_probe(C.byref(P), mi, mj, dv, m0, u, C.byref(k))
+    return mn, int(k.value)

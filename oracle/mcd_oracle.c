@@ -78,6 +78,8 @@ typedef struct {
     double mu, sigma_h2, dm_group, frag_xi, erosion_chi;
     /* constant-kernel (0D) mode and initial state overrides */
     double K_const, V_const, m_init, M_total;
+    /* fragmentation probability ramp: relative width below v_frag (reading) */
+    double frag_ramp;
     int32_t kernel_mode; /* 0 physical, 1 constant kernel */
     int32_t settle_form; /* 0: v_z = -z Omega St ; 1: -z Omega St/(1+St) */
     int32_t dv_flags;    /* ORC_DV_* mask */
@@ -350,6 +352,15 @@ static double orc_fragment(const orc_params *P, double m0, double mmax, double u
 
 double orc_fragment_probe(const orc_params *P, double m0, double mmax, double u) { return orc_fragment(P, m0, mmax, u); }
 
+static double orc_outcome(const orc_params *P, double mi, double mj, double dv, double m0, double u, int *kind);
+double orc_outcome_probe(const orc_params *P, double mi, double mj, double dv, double m0, double u, int32_t *kind)
+{
+    int k = 0;
+    const double mn = orc_outcome(P, mi, mj, dv, m0, u, &k);
+    *kind = k;
+    return mn;
+}
+
 static double orc_monomer_mass(const orc_params *P)
 {
     if (P->m_init > 0.0) return P->m_init;
@@ -365,11 +376,26 @@ typedef struct {
 } orc_event;
 
 /* outcome of representative i meeting a particle of swarm j; returns m_i new */
+/* Outcome of representative i meeting a particle of swarm j at relative
+ * velocity dv, u the event's fourth uniform.  Below v_frag the pair sticks;
+ * with frag_ramp = delta > 0 (reading: a linear ramp, the paper names the
+ * outcomes but not their parameters) the fragmentation probability rises
+ * linearly from 0 at v_lo = v_frag (1 - delta) to 1 at v_frag, decided by
+ * u < p, and u / p (uniform again) then draws the fragment. */
 static double orc_outcome(const orc_params *P, double mi, double mj, double dv, double m0, double u, int *kind)
 {
     double gain = mj;
     if (P->dm_group > 0.0 && P->dm_group * mi > mj) gain = P->dm_group * mi; /* N_g m_j */
-    if (P->kernel_mode == 1 || dv < P->v_frag) {
+    const double vlo = P->v_frag * (1.0 - P->frag_ramp);
+    int stick = P->kernel_mode == 1 || dv < vlo;
+    if (!stick && dv < P->v_frag) {
+        const double p = (dv - vlo) / (P->v_frag - vlo);
+        if (u < p)
+            u = u / p;
+        else
+            stick = 1;
+    }
+    if (stick) {
         *kind = 0;
         return mi + gain;
     }

@@ -28,7 +28,7 @@ def benchmark_disk(**over) -> dict:
         sigma0=1000.0, p=1.0, T0=280.0, q=0.5, alpha=1e-3, v_frag=1000.0, erosion_ratio=10.0,
         dust_to_gas=0.01, r_in=1.0 * AU, r_out=100.0 * AU, m_star=1.0, rho_s=1.6, a_mono=1e-4,
         mu=2.34, sigma_h2=2e-15, dm_group=1e-3, frag_xi=11.0 / 6.0, erosion_chi=1.0,
-        K_const=1.0, V_const=1.0, m_init=0.0, M_total=0.0,
+        K_const=1.0, V_const=1.0, m_init=0.0, M_total=0.0, frag_ramp=0.0,
         kernel_mode=0, settle_form=0, dv_flags=DV_ALL, tr_flags=TR_RADIAL | TR_VERTICAL,
     )
     d.update(over)

@@ -641,3 +641,30 @@ def test_sigma_map_matches_brute_force():
     # every particle inside both ranges is counted once
     inside = (r >= r_edges[0]) & (r < r_edges[-1]) & (m >= m_edges[0]) & (m < m_edges[-1])
     assert math.isclose(got.sum(), math.fsum(M[inside]), rel_tol=1e-13)
+
+
+def test_outcome_fragmentation_ramp():
+    """A ramp of relative width delta below v_frag: no fragmentation below
+    v_frag (1 - delta), always at v_frag and above, and in between exactly the
+    share p = (dv - v_lo) / (v_frag - v_lo) of a uniform u-grid fragments, each
+    with the fragment draw at u / p; delta = 0 is the sharp threshold."""
+    m0 = 4 / 3 * np.pi * 1.6 * 1e-12
+    mi, mj = 2e-3, 1.5e-3  # comparable masses: fragmentation, not erosion
+    P = W.benchmark_disk(v_frag=1000.0, frag_ramp=0.4, dm_group=0.0)
+    vlo = 1000.0 * (1.0 - 0.4)
+    us = (np.arange(4000) + 0.5) / 4000
+    for dv, p in ((599.0, 0.0), (vlo, 0.0), (700.0, (700.0 - vlo) / (1000.0 - vlo)), (950.0, (950.0 - vlo) / 400.0),
+                  (1000.0, 1.0), (5000.0, 1.0)):
+        res = [oracle.outcome(P, mi, mj, dv, m0, u) for u in us]
+        kinds = np.array([k for _, k in res])
+        assert np.sum(kinds == 1) == np.sum(us < p)
+        assert np.all(kinds[us >= p] == 0)
+        for u, (mn, k) in zip(us, res):
+            if k == 1:
+                assert mn == oracle.fragment(P, m0, max(mi, mj), u / p if p < 1.0 else u)
+            else:
+                assert mn == mi + mj
+    # delta = 0: the sharp threshold
+    P0r = W.benchmark_disk(v_frag=1000.0, frag_ramp=0.0, dm_group=0.0)
+    assert oracle.outcome(P0r, mi, mj, 999.999, m0, 0.1)[1] == 0
+    assert oracle.outcome(P0r, mi, mj, 1000.0, m0, 0.1)[1] == 1
