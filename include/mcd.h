@@ -82,6 +82,8 @@ typedef struct {
     double dust_to_gas, r_in, r_out, m_star, rho_s, a_mono;
     double mu, sigma_h2, dm_group, frag_xi, erosion_chi;
     double K_const, V_const, m_init, M_total;
+    double frag_ramp; /* fragmentation probability: 0 below v_frag (1 - frag_ramp), 1 from v_frag, linear
+                         between (0 = the sharp threshold); 0 <= frag_ramp < 1 */
     int32_t kernel_mode, settle_form, dv_flags, tr_flags;
 } mcd_disk_params;
 

@@ -45,6 +45,7 @@ int plan(const mcd_disk_params *p, const mcd_grid *g, int32_t nd, Sizes &S)
         if (G.n_r <= 0 || G.n_z <= 0 || G.per_cell <= 0) return MCD_EINVAL;
         if (G.per_cell > kMaxCell) return MCD_EINVAL;
         if ((int64_t)G.n_z * G.per_cell > kZoneCap) return MCD_EINVAL;
+        if (!(P.frag_ramp >= 0.0 && P.frag_ramp < 1.0)) return MCD_EINVAL;
         if (P.kernel_mode == 1) {
             if (!(P.V_const > 0.0) || !(P.m_init > 0.0)) return MCD_EINVAL;
         } else if (P.kernel_mode == 0) {
@@ -213,6 +214,8 @@ int mcd_init_disk(mcd_ctx **out, const mcd_disk_params *p, const mcd_grid *g, in
     c->stream = (cudaStream_t)stream;
     c->seed = seed;
     c->hp.assign(p, p + n_disks);
+    for (int32_t d = 0; d < n_disks; ++d)
+        if (p[d].frag_ramp > 0.0) c->ramp = 1;
     c->hg.assign(g, g + n_disks);
     c->hd = S.disks;
     c->N = S.N;

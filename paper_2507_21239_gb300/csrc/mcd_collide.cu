@@ -463,7 +463,7 @@ struct Frag<float> {
 
 // new mass of representative i after meeting a particle of swarm j; dmmi is
 // dm m_i (0 when grouping is off), computed ahead by the caller; mih, mjh the
-// hi parts of the masses (FP32 path)
+// hi parts of the masses (FP32 path).  u3 draws a fragment's mass.
 template <class T>
 __device__ __forceinline__ double outcome(const CellK<T> &c, double mi, double mj, T mih, T mjh, double dmmi, T dv,
                                           T u3, int &kind)
@@ -485,6 +485,21 @@ __device__ __forceinline__ double outcome(const CellK<T> &c, double mi, double m
     }
     kind = 1;
     return Frag<T>::draw(c, big, igt ? mih : mjh, u3);
+}
+
+// The same with a fragmentation ramp below v_frag: the probability of
+// fragmenting rises linearly from 0 at vlo = v_frag (1 - frag_ramp) to 1 at
+// v_frag, decided by u3 < p; u3 / p (uniform again) then draws the fragment.
+template <class T>
+__device__ __forceinline__ double outcome_ramp(const CellK<T> &c, double mi, double mj, T mih, T mjh, double dmmi,
+                                               T dv, T u3, T vlo, int &kind)
+{
+    const T vfr = sizeof(T) == 4 ? (T)c.vfrag_t : (T)c.vfrag;
+    if (c.kmode != 1 && dv < vfr && !(dv < vlo)) {  // inside the ramp
+        const T p = fdiv(dv - vlo, vfr - vlo);
+        if (u3 < p) return outcome<T>(c, mi, mj, mih, mjh, dmmi, vfr, fdiv(u3, p), kind);  // fragments as at v_frag
+    }
+    return outcome<T>(c, mi, mj, mih, mjh, dmmi, dv, u3, kind);
 }
 
 // ---- accumulators: FP64 sum, or a compensated FP32 pair ------------------------
@@ -606,7 +621,7 @@ __global__ void k_cellconst(const mcd_disk_params *params, const int32_t *cell_d
 // event is then read, not recomputed, and later full rebuilds sum stored
 // entries; pair_dv is symmetric bit for bit, so the results are those of the
 // recomputing path.
-template <class T, bool STORE>
+template <class T, bool STORE, bool RAMP>
 __global__ void __launch_bounds__(kMaxCell) k_collide(CollideArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -767,8 +782,15 @@ __global__ void __launch_bounds__(kMaxCell) k_collide(CollideArgs A)
             // only the stores wait for the crossing test
             const double tn = sh.t + (double)fdiv(dr.L, tot);
             int kind = 0;
-            const double mnew = outcome<T>(c, mi, msh[j], pi.mh, parts[j].mh, dmmi, STORE ? Dm[i * ld + j] : dvrow[j],
-                                           dr.u3, kind);
+            double mnew;
+            if constexpr (RAMP) {  // the ramp's foot as the plain FP64 evaluation forms it
+                const mcd_disk_params &P = A.params[disk];
+                mnew = outcome_ramp<T>(c, mi, msh[j], pi.mh, parts[j].mh, dmmi, STORE ? Dm[i * ld + j] : dvrow[j],
+                                       dr.u3, (T)(P.v_frag * (1.0 - P.frag_ramp)), kind);
+            } else {
+                mnew = outcome<T>(c, mi, msh[j], pi.mh, parts[j].mh, dmmi, STORE ? Dm[i * ld + j] : dvrow[j], dr.u3,
+                                  kind);
+            }
             const Part<T> pnew = make_part<T>(c, mnew, pi.Mv);
             const int stop = tn >= t_end;
             if (!stop) {
@@ -974,15 +996,18 @@ static cudaError_t collide_impl(mcd_ctx *cx, int from_state, double t_end)
     const size_t smem_store = collide_smem<T>(nthr) + (size_t)ld * ld * sizeof(T);
     const bool store = sizeof(T) == 4 && cx->dv_matrix && smem_store <= (size_t)cx->smem_optin;
     A.dv_ld = ld;
+    // a fragmentation ramp in any disk selects the kernel variant with its branch
+    auto go = [&](auto kernel, size_t bytes) {
+        kernel<<<(unsigned)cx->C, nthr, bytes, cx->stream>>>(A);
+        cx->launches += 2;
+        return cudaGetLastError();
+    };
     if constexpr (sizeof(T) == 4)
         if (store) {
-            k_collide<T, true><<<(unsigned)cx->C, nthr, smem_store > smem ? smem_store : smem, cx->stream>>>(A);
-            cx->launches += 2;
-            return cudaGetLastError();
+            const size_t b = smem_store > smem ? smem_store : smem;
+            return cx->ramp ? go(k_collide<T, true, true>, b) : go(k_collide<T, true, false>, b);
         }
-    k_collide<T, false><<<(unsigned)cx->C, nthr, smem, cx->stream>>>(A);
-    cx->launches += 2;
-    return cudaGetLastError();
+    return cx->ramp ? go(k_collide<T, false, true>, smem) : go(k_collide<T, false, false>, smem);
 }
 
 // the dynamic shared memory each variant may request; for the stored-matrix
@@ -991,8 +1016,10 @@ template <class T>
 static cudaError_t prepare_impl(mcd_ctx *c)
 {
     size_t need = collide_smem<T>(kMaxCell);
-    cudaError_t e = cudaFuncSetAttribute(k_collide<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(need > kExclusiveSmem ? need : kExclusiveSmem));
+    const int want = (int)(need > kExclusiveSmem ? need : kExclusiveSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_collide<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_collide<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
     c->smem_optin = 0;
     if constexpr (sizeof(T) != 4) {
         return e;
@@ -1002,11 +1029,15 @@ static cudaError_t prepare_impl(mcd_ctx *c)
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
             return e;
-        cudaFuncAttributes fa;
-        if ((e = cudaFuncGetAttributes(&fa, k_collide<T, true>)) != cudaSuccess) return e;
-        const int dyn = optin - (int)fa.sharedSizeBytes;
+        cudaFuncAttributes fa, fr;
+        if ((e = cudaFuncGetAttributes(&fa, k_collide<T, true, false>)) != cudaSuccess) return e;
+        if ((e = cudaFuncGetAttributes(&fr, k_collide<T, true, true>)) != cudaSuccess) return e;
+        const int st = (int)(fa.sharedSizeBytes > fr.sharedSizeBytes ? fa.sharedSizeBytes : fr.sharedSizeBytes);
+        const int dyn = optin - st;
         if (dyn <= 0) return cudaSuccess;
-        e = cudaFuncSetAttribute(k_collide<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        e = cudaFuncSetAttribute(k_collide<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_collide<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
         if (e == cudaSuccess) c->smem_optin = dyn;
         return e;
     }

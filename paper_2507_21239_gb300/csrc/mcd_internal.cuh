@@ -218,6 +218,7 @@ struct mcd_ctx {
     int64_t rebuild_every = 0;
     int32_t use_graph = 1, dump_R = 0, lpt = 1, threads = 0, exclusive = 1, dv_matrix = 1;
     int32_t smem_optin = 0;  // dynamic shared memory the stored-dv collide variant may request
+    int32_t ramp = 0;        // some disk has a fragmentation ramp (frag_ramp > 0)
     int64_t log_cell = -1;
 
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};

@@ -33,14 +33,15 @@ class mcd_disk_params(C.Structure):
         "sigma0", "p", "T0", "q", "alpha", "v_frag", "erosion_ratio",
         "dust_to_gas", "r_in", "r_out", "m_star", "rho_s", "a_mono",
         "mu", "sigma_h2", "dm_group", "frag_xi", "erosion_chi",
-        "K_const", "V_const", "m_init", "M_total")] + [
+        "K_const", "V_const", "m_init", "M_total", "frag_ramp")] + [
         (n, C.c_int32) for n in ("kernel_mode", "settle_form", "dv_flags", "tr_flags")]
+    OPTIONAL = {"frag_ramp": 0.0}  # keys a caller's dict may leave out
 
     @classmethod
     def from_dict(cls, d: dict) -> "mcd_disk_params":
         p = cls()
         for name, _ in cls._fields_:
-            setattr(p, name, d[name])
+            setattr(p, name, d[name] if name in d or name not in cls.OPTIONAL else cls.OPTIONAL[name])
         return p
 
 

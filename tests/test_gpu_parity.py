@@ -234,16 +234,21 @@ def _one_cell(P, n, seed, prec, masses, r_au=1.3, M=None):
     return d, cell, b[0], V[0]
 
 
-@pytest.mark.parametrize("mode,n,vfrag,dm", [("phys", 50, 300.0, 1e-3), ("phys", 200, 1000.0, 1e-2),
-                                             ("phys", 96, 30.0, 0.0), ("const", 200, 0, 0)])
-def test_event_sequence_fp64(mode, n, vfrag, dm):
+@pytest.mark.parametrize("mode,n,vfrag,dm,extra", [
+    ("phys", 50, 300.0, 1e-3, {}), ("phys", 200, 1000.0, 1e-2, {}), ("phys", 96, 30.0, 0.0, {}),
+    ("const", 200, 0, 0, {}),
+    # outcome variants: a fragmentation ramp, another fragment slope xi, another erosion efficiency chi
+    ("phys", 120, 100.0, 1e-3, {"frag_ramp": 0.6}),
+    ("phys", 120, 60.0, 1e-3, {"frag_ramp": 0.3, "frag_xi": 1.5, "erosion_chi": 0.5}),
+], ids=["vf300", "vf1000", "vf30", "const", "ramp", "ramp_xi_chi"])
+def test_event_sequence_fp64(mode, n, vfrag, dm, extra):
     """Same keys, FP64: the GPU event chain is the oracle's, event by event."""
     seed = 21
     if mode == "const":
         P = W.constant_kernel_cell()
         masses = np.ones(n)
     else:
-        P = W.benchmark_disk(v_frag=vfrag, dm_group=dm)
+        P = W.benchmark_disk(v_frag=vfrag, dm_group=dm, **extra)
         masses = W.random_masses(n, seed=3, lo=1e-11, hi=1e-1, ties=0.2)
     d, cell, b, V = _one_cell(P, n, seed, mcd.MCD_FP64, masses, M=np.full(n, 1.0 / n) if mode == "const" else None)
     Vo = V if mode == "phys" else 1.0
