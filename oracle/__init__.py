@@ -104,6 +104,15 @@ def lib():
                               C.c_double, C.c_int64, C.c_int64, C.c_uint64, C.c_uint64, C.c_int64, C.c_int64,
                               _d, _i64, C.c_int32]
         L.orc_moments.argtypes = [C.c_int64, _d, _d, _d, C.c_int32, _d, _d]
+        L.orc_tracer_update.argtypes = [_P(Params), C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                        C.c_int32]
+        L.orc_tracer_update.restype = C.c_double
+        L.orc_collide_cell_q.argtypes = [_P(Params), C.c_double, C.c_double, C.c_double, C.c_int64, _d, _d, _d,
+                                         C.c_double, C.c_double, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64,
+                                         C.c_int64, C.c_int64, _i64, _d, _P(Event), C.c_int64]
+        L.orc_run_q.argtypes = [_P(Params), C.c_int32, C.c_int32, C.c_int64, _d, _d, _d, _d, _u32, _d, C.c_double,
+                                C.c_double, C.c_int64, C.c_int64, C.c_uint64, C.c_uint64, C.c_int64, C.c_int64,
+                                _d, _i64, C.c_int32]
         L.orc_sigma_map.argtypes = [C.c_int64, _d, _d, _d, C.c_int32, _d, C.c_int32, _d, _d]
         _lib = L
     return _lib
@@ -201,14 +210,15 @@ def collide_cell(params: dict, rc, zc, V, m, M, t0, t_end, seed, disk, step, cel
 class DiskState:
     """SoA particle state of one disk (oracle side)."""
 
-    def __init__(self, m, M, r, z, id_):
+    def __init__(self, m, M, r, z, id_, q=None):
         self.m, self.M, self.r, self.z = _f64(m).copy(), _f64(M).copy(), _f64(r).copy(), _f64(z).copy()
         self.id = np.ascontiguousarray(id_, dtype=np.uint32).copy()
+        self.q = None if q is None else _f64(q).copy()  # optional tracer column
         self.accreted = 0.0
         self.events = 0
 
     def copy(self):
-        s = DiskState(self.m, self.M, self.r, self.z, self.id)
+        s = DiskState(self.m, self.M, self.r, self.z, self.id, self.q)
         s.accreted, s.events = self.accreted, self.events
         return s
 
@@ -236,6 +246,8 @@ def regrid(params: dict, n_r: int, n_z: int, s: DiskState):
                           _ptr(s.r, C.c_double), _ptr(s.z, C.c_double), _ptr(s.id, C.c_uint32),
                           _ptr(perm, C.c_int64), _ptr(off, C.c_int64), _ptr(cb, C.c_double), _ptr(cv, C.c_double),
                           _ptr(na, C.c_int64))
+    if s.q is not None and st == 0:
+        s.q = s.q[perm].copy()  # the tracer follows its particle
     return st, perm, off, cb, cv, int(na[0])
 
 
@@ -264,9 +276,16 @@ def run(params: dict, n_r: int, n_z: int, s: DiskState, t0: float, dt: float, st
     acc = np.zeros(1)
     ev = np.zeros(1, np.int64)
     P = Params.from_dict(params)
-    st = lib().orc_run(C.byref(P), n_r, n_z, s.m.size, _ptr(s.m, C.c_double), _ptr(s.M, C.c_double),
-                       _ptr(s.r, C.c_double), _ptr(s.z, C.c_double), _ptr(s.id, C.c_uint32), t0, dt, step0, n_steps,
-                       seed, disk, max_events, rebuild_every, _ptr(acc, C.c_double), _ptr(ev, C.c_int64), nthreads)
+    if s.q is None:
+        st = lib().orc_run(C.byref(P), n_r, n_z, s.m.size, _ptr(s.m, C.c_double), _ptr(s.M, C.c_double),
+                           _ptr(s.r, C.c_double), _ptr(s.z, C.c_double), _ptr(s.id, C.c_uint32), t0, dt, step0,
+                           n_steps, seed, disk, max_events, rebuild_every, _ptr(acc, C.c_double),
+                           _ptr(ev, C.c_int64), nthreads)
+    else:
+        st = lib().orc_run_q(C.byref(P), n_r, n_z, s.m.size, _ptr(s.m, C.c_double), _ptr(s.M, C.c_double),
+                             _ptr(s.r, C.c_double), _ptr(s.z, C.c_double), _ptr(s.id, C.c_uint32),
+                             _ptr(s.q, C.c_double), t0, dt, step0, n_steps, seed, disk, max_events, rebuild_every,
+                             _ptr(acc, C.c_double), _ptr(ev, C.c_int64), nthreads)
     s.accreted += float(acc[0])
     s.events += int(ev[0])
     return st
@@ -299,3 +318,27 @@ def outcome(params: dict, mi: float, mj: float, dv: float, m0: float, u: float):
     P = Params.from_dict(params)
     mn = lib().orc_outcome_probe(C.byref(P), mi, mj, dv, m0, u, C.byref(k))
     return mn, int(k.value)
+
+
+def tracer_update(params: dict, mi, mj, qi, qj, mnew, kind) -> float:
+    """The tracer of representative i after one event of the given kind."""
+    P = Params.from_dict(params)
+    return lib().orc_tracer_update(C.byref(P), mi, mj, qi, qj, mnew, kind)
+
+
+def collide_cell_q(params: dict, rc, zc, V, m, M, q, t0, t_end, seed, disk, step, cell,
+                   max_events=NO_CAP, rebuild_every=0, log_cap=0):
+    """collide_cell carrying the tracer column; returns (status, m_new, q_new, events, R, log)."""
+    m, M, q = _f64(m).copy(), _f64(M), _f64(q).copy()
+    n = m.size
+    ev = np.zeros(1, np.int64)
+    R = np.zeros(n)
+    log = (Event * max(log_cap, 1))()
+    P = Params.from_dict(params)
+    st = lib().orc_collide_cell_q(C.byref(P), rc, zc, V, n, _ptr(m, C.c_double), _ptr(M, C.c_double),
+                                  _ptr(q, C.c_double), t0, t_end, seed, disk, step, cell, max_events, rebuild_every,
+                                  _ptr(ev, C.c_int64), _ptr(R, C.c_double), log if log_cap > 0 else None, log_cap)
+    k = int(min(ev[0], log_cap))
+    lg = np.array([(log[e].i, log[e].j, log[e].outcome, log[e].t, log[e].m_new) for e in range(k)],
+                  dtype=[("i", "i4"), ("j", "i4"), ("outcome", "i4"), ("t", "f8"), ("m_new", "f8")])
+    return st, m, q, int(ev[0]), R, lg

@@ -412,10 +412,29 @@ static double orc_outcome(const orc_params *P, double mi, double mj, double dv, 
     return orc_fragment(P, m0, big, u);
 }
 
-int orc_collide_cell(const orc_params *P, double rc, double zc, double V, int64_t n, double *m, const double *M,
-                     double t0, double t_end, uint64_t seed, uint64_t disk, uint64_t step, uint64_t cell,
-                     int64_t max_events, int64_t rebuild_every, int64_t *events_out, double *R_out,
-                     orc_event *evlog, int64_t log_cap)
+/* A tracked property of each swarm (a composition fraction q), carried by its
+ * representative particle (SURVEY's extra tracked properties; reading, the
+ * paper gives no rule): sticking mixes by mass, q_i <- (m_i q_i + g q_j) /
+ * (m_i + g), g = N_g m_j the absorbed mass; fragmentation gives the pair's
+ * mass-weighted mixture; erosion leaves the larger body's q as it was and turns
+ * the smaller one into debris of itself and the chipped mass, chi times its own:
+ * (q_i + chi q_j) / (1 + chi).  mi, mj before the event; mnew after it. */
+double orc_tracer_update(const orc_params *P, double mi, double mj, double qi, double qj, double mnew, int32_t kind)
+{
+    if (kind == 0) {
+        double gain = mj;
+        if (P->dm_group > 0.0 && P->dm_group * mi > mj) gain = P->dm_group * mi;
+        return (mi * qi + gain * qj) / mnew;
+    }
+    if (kind == 1) return (mi * qi + mj * qj) / (mi + mj);
+    if (mi >= mj) return qi;
+    return (qi + P->erosion_chi * qj) / (1.0 + P->erosion_chi);
+}
+
+static int orc_collide_cell_impl(const orc_params *P, double rc, double zc, double V, int64_t n, double *m,
+                                 const double *M, double *q, double t0, double t_end, uint64_t seed, uint64_t disk,
+                                 uint64_t step, uint64_t cell, int64_t max_events, int64_t rebuild_every,
+                                 int64_t *events_out, double *R_out, orc_event *evlog, int64_t log_cap)
 {
     int status = ORC_OK;
     int64_t ev = 0;
@@ -490,6 +509,7 @@ int orc_collide_cell(const orc_params *P, double rc, double zc, double V, int64_
             evlog[ev].i = (int32_t)i; evlog[ev].j = (int32_t)j; evlog[ev].outcome = kind;
             evlog[ev].t = t; evlog[ev].m_new = mnew;
         }
+        if (q) q[i] = orc_tracer_update(P, pt[i].m, pt[j].m, q[i], q[j], mnew, kind);
         pt[i] = orc_particle(P, &g, mnew);
         /* only row i and column i change: R_k += r_ki(new) - r_ki(old), R_i afresh */
         double Rin = 0.0;
@@ -511,6 +531,25 @@ int orc_collide_cell(const orc_params *P, double rc, double zc, double V, int64_
     if (events_out) *events_out = ev;
     free(pt); free(R); free(row); free(colo);
     return status;
+}
+
+int orc_collide_cell(const orc_params *P, double rc, double zc, double V, int64_t n, double *m, const double *M,
+                     double t0, double t_end, uint64_t seed, uint64_t disk, uint64_t step, uint64_t cell,
+                     int64_t max_events, int64_t rebuild_every, int64_t *events_out, double *R_out,
+                     orc_event *evlog, int64_t log_cap)
+{
+    return orc_collide_cell_impl(P, rc, zc, V, n, m, M, NULL, t0, t_end, seed, disk, step, cell, max_events,
+                                 rebuild_every, events_out, R_out, evlog, log_cap);
+}
+
+/* the same with the tracer column q (updated in place) */
+int orc_collide_cell_q(const orc_params *P, double rc, double zc, double V, int64_t n, double *m, const double *M,
+                       double *q, double t0, double t_end, uint64_t seed, uint64_t disk, uint64_t step, uint64_t cell,
+                       int64_t max_events, int64_t rebuild_every, int64_t *events_out, double *R_out,
+                       orc_event *evlog, int64_t log_cap)
+{
+    return orc_collide_cell_impl(P, rc, zc, V, n, m, M, q, t0, t_end, seed, disk, step, cell, max_events,
+                                 rebuild_every, events_out, R_out, evlog, log_cap);
 }
 
 /* ======================================================================== */
@@ -730,10 +769,10 @@ void orc_transport(const orc_params *P, int64_t N, double *r, double *z, const d
 /* ======================================================================== */
 /* Whole-disk driver: regrid -> collide every cell to t + dt -> transport.  */
 /* ======================================================================== */
-int orc_collide_all(const orc_params *P, int32_t n_r, int32_t n_z, const int64_t *cell_off, const double *cell_b,
-                    const double *cell_V, double *m, const double *M, double t0, double t_end, uint64_t seed,
-                    uint64_t disk, uint64_t step, int64_t max_events, int64_t rebuild_every, int64_t *cell_events,
-                    int32_t nthreads)
+static int orc_collide_all_impl(const orc_params *P, int32_t n_r, int32_t n_z, const int64_t *cell_off,
+                                const double *cell_b, const double *cell_V, double *m, const double *M, double *q,
+                                double t0, double t_end, uint64_t seed, uint64_t disk, uint64_t step,
+                                int64_t max_events, int64_t rebuild_every, int64_t *cell_events, int32_t nthreads)
 {
     int64_t ncell = (int64_t)n_r * n_z;
     int status = ORC_OK;
@@ -743,8 +782,9 @@ int orc_collide_all(const orc_params *P, int32_t n_r, int32_t n_z, const int64_t
 #endif
     for (int64_t c = 0; c < ncell; ++c) {
         int64_t off = cell_off[c], n = cell_off[c + 1] - cell_off[c], ev = 0;
-        int st = orc_collide_cell(P, cell_b[6 * c + 4], cell_b[6 * c + 5], cell_V[c], n, m + off, M + off, t0, t_end,
-                                  seed, disk, step, (uint64_t)c, max_events, rebuild_every, &ev, NULL, NULL, 0);
+        int st = orc_collide_cell_impl(P, cell_b[6 * c + 4], cell_b[6 * c + 5], cell_V[c], n, m + off, M + off,
+                                       q ? q + off : NULL, t0, t_end, seed, disk, step, (uint64_t)c, max_events,
+                                       rebuild_every, &ev, NULL, NULL, 0);
         if (cell_events) cell_events[c] = ev;
         if (st != ORC_OK) {
 #ifdef _OPENMP
@@ -756,33 +796,67 @@ int orc_collide_all(const orc_params *P, int32_t n_r, int32_t n_z, const int64_t
     return status;
 }
 
-/* n_steps steps of length dt from time t0 and step index step0 */
-int orc_run(const orc_params *P, int32_t n_r, int32_t n_z, int64_t N, double *m, double *M, double *r, double *z,
-            uint32_t *id, double t0, double dt, int64_t step0, int64_t n_steps, uint64_t seed, uint64_t disk,
-            int64_t max_events, int64_t rebuild_every, double *accreted, int64_t *events_total, int32_t nthreads)
+int orc_collide_all(const orc_params *P, int32_t n_r, int32_t n_z, const int64_t *cell_off, const double *cell_b,
+                    const double *cell_V, double *m, const double *M, double t0, double t_end, uint64_t seed,
+                    uint64_t disk, uint64_t step, int64_t max_events, int64_t rebuild_every, int64_t *cell_events,
+                    int32_t nthreads)
+{
+    return orc_collide_all_impl(P, n_r, n_z, cell_off, cell_b, cell_V, m, M, NULL, t0, t_end, seed, disk, step,
+                                max_events, rebuild_every, cell_events, nthreads);
+}
+
+/* n_steps steps of length dt from time t0 and step index step0; q (or NULL)
+ * is the tracer column, reordered with the particles by every regrid */
+static int orc_run_impl(const orc_params *P, int32_t n_r, int32_t n_z, int64_t N, double *m, double *M, double *r,
+                        double *z, uint32_t *id, double *q, double t0, double dt, int64_t step0, int64_t n_steps,
+                        uint64_t seed, uint64_t disk, int64_t max_events, int64_t rebuild_every, double *accreted,
+                        int64_t *events_total, int32_t nthreads)
 {
     int64_t ncell = (int64_t)n_r * n_z;
     int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (ncell + 1));
     double *cb = (double *)malloc(sizeof(double) * 6 * ncell);
     double *cv = (double *)malloc(sizeof(double) * ncell);
     int64_t *ce = (int64_t *)malloc(sizeof(int64_t) * ncell);
+    int64_t *perm = q ? (int64_t *)malloc(sizeof(int64_t) * N) : NULL;
+    double *qt = q ? (double *)malloc(sizeof(double) * N) : NULL;
     int status = ORC_OK;
     double t = t0;
     for (int64_t s = 0; s < n_steps && status == ORC_OK; ++s) {
         uint64_t step = (uint64_t)(step0 + s);
         int64_t na = 0;
-        status = orc_regrid(P, n_r, n_z, N, m, M, r, z, id, NULL, off, cb, cv, &na);
+        status = orc_regrid(P, n_r, n_z, N, m, M, r, z, id, perm, off, cb, cv, &na);
         if (status != ORC_OK) break;
-        status = orc_collide_all(P, n_r, n_z, off, cb, cv, m, M, t, t + dt, seed, disk, step, max_events,
-                                 rebuild_every, ce, nthreads);
+        if (q) {
+            for (int64_t k = 0; k < N; ++k) qt[k] = q[perm[k]];
+            memcpy(q, qt, sizeof(double) * N);
+        }
+        status = orc_collide_all_impl(P, n_r, n_z, off, cb, cv, m, M, q, t, t + dt, seed, disk, step, max_events,
+                                      rebuild_every, ce, nthreads);
         for (int64_t c = 0; c < ncell; ++c)
             if (events_total) *events_total += ce[c];
         if (P->kernel_mode == 0 && (P->tr_flags & (ORC_TR_RADIAL | ORC_TR_VERTICAL)))
             orc_transport(P, N, r, z, m, M, id, dt, seed, disk, step, accreted);
         t += dt;
     }
-    free(off); free(cb); free(cv); free(ce);
+    free(off); free(cb); free(cv); free(ce); free(perm); free(qt);
     return status;
+}
+
+int orc_run(const orc_params *P, int32_t n_r, int32_t n_z, int64_t N, double *m, double *M, double *r, double *z,
+            uint32_t *id, double t0, double dt, int64_t step0, int64_t n_steps, uint64_t seed, uint64_t disk,
+            int64_t max_events, int64_t rebuild_every, double *accreted, int64_t *events_total, int32_t nthreads)
+{
+    return orc_run_impl(P, n_r, n_z, N, m, M, r, z, id, NULL, t0, dt, step0, n_steps, seed, disk, max_events,
+                        rebuild_every, accreted, events_total, nthreads);
+}
+
+int orc_run_q(const orc_params *P, int32_t n_r, int32_t n_z, int64_t N, double *m, double *M, double *r, double *z,
+              uint32_t *id, double *q, double t0, double dt, int64_t step0, int64_t n_steps, uint64_t seed,
+              uint64_t disk, int64_t max_events, int64_t rebuild_every, double *accreted, int64_t *events_total,
+              int32_t nthreads)
+{
+    return orc_run_impl(P, n_r, n_z, N, m, M, r, z, id, q, t0, dt, step0, n_steps, seed, disk, max_events,
+                        rebuild_every, accreted, events_total, nthreads);
 }
 
 /* ---- diagnostics --------------------------------------------------------

@@ -668,3 +668,47 @@ def test_outcome_fragmentation_ramp():
     P0r = W.benchmark_disk(v_frag=1000.0, frag_ramp=0.0, dm_group=0.0)
     assert oracle.outcome(P0r, mi, mj, 999.999, m0, 0.1)[1] == 0
     assert oracle.outcome(P0r, mi, mj, 1000.0, m0, 0.1)[1] == 1
+
+
+# ---- a tracked property (tracer) per swarm ---------------------------------
+def test_tracer_rules_closed_forms():
+    """Hand-computed two-particle cases of each outcome kind."""
+    P = W.benchmark_disk(dm_group=0.0, erosion_chi=1.0)
+    assert oracle.tracer_update(P, 2.0, 1.0, 0.0, 1.0, 3.0, 0) == pytest.approx(1.0 / 3.0, rel=1e-15)
+    Pg = W.benchmark_disk(dm_group=1.0)  # grouping: i absorbs dm m_i = 2 > m_j
+    assert oracle.tracer_update(Pg, 2.0, 1.0, 0.0, 1.0, 4.0, 0) == pytest.approx(0.5, rel=1e-15)
+    assert oracle.tracer_update(P, 1.0, 3.0, 1.0, 0.0, 0.7, 1) == pytest.approx(0.25, rel=1e-15)
+    assert oracle.tracer_update(P, 50.0, 1.0, 0.2, 0.8, 49.0, 2) == 0.2  # the larger body keeps its own
+    assert oracle.tracer_update(P, 1.0, 50.0, 0.2, 0.8, 0.3, 2) == pytest.approx(0.5, rel=1e-15)
+    Pc = W.benchmark_disk(erosion_chi=0.5)
+    assert oracle.tracer_update(Pc, 1.0, 50.0, 0.2, 0.8, 0.3, 2) == pytest.approx(0.4, rel=1e-15)
+
+
+def test_tracer_in_event_chains():
+    """Over a cell's event chain with all three outcomes: a uniform tracer stays
+    uniform, every value stays inside the initial range (each update is a
+    convex mixture), and the tracer leaves masses and events unchanged."""
+    P = W.benchmark_disk(v_frag=30.0, dm_group=1e-3)
+    n = 60
+    m = W.random_masses(n, seed=9, lo=1e-6, hi=1e-2)
+    M = np.full(n, 1e26)
+    rc, zc, V = 1.2 * AU, 0.0, 1e39
+    R = oracle.rate_matrix(P, rc, zc, V, m, M)[1]
+    t_end = 3000.0 / R.sum()
+    st0, m0_, ev0, _, lg = oracle.collide_cell(P, rc, zc, V, m, M, 0.0, t_end, 3, 0, 0, 0, log_cap=100000)
+    assert ev0 > 1000 and len(set(lg["outcome"])) == 3
+    st, mq, q, ev, _, _ = oracle.collide_cell_q(P, rc, zc, V, m, M, np.full(n, 0.37), 0.0, t_end, 3, 0, 0, 0)
+    assert st == 0 and ev == ev0 and np.array_equal(mq, m0_)
+    assert np.allclose(q, 0.37, rtol=1e-14, atol=0)
+    q0 = np.random.default_rng(2).uniform(0.1, 0.9, n)
+    _, _, q, _, _, _ = oracle.collide_cell_q(P, rc, zc, V, m, M, q0, 0.0, t_end, 3, 0, 0, 0)
+    assert q.min() >= q0.min() * (1 - 1e-14) and q.max() <= q0.max() * (1 + 1e-14)
+    assert not np.array_equal(q, q0)
+
+
+def test_tracer_follows_its_particle_through_regrid():
+    N = 300
+    s = oracle.init_disk(P0, N, seed=4)
+    s.q = s.id.astype(float) / N
+    st = oracle.regrid(P0, 5, 3, s)[0]
+    assert st == 0 and np.array_equal(s.q, s.id.astype(float) / N)
