@@ -117,6 +117,8 @@ typedef struct mcd_ctx mcd_ctx;
 #define MCD_OPT_DV_MATRIX 10    /* 1: MCD_MIXED keeps each cell's dv_ij matrix in shared memory when it fits
                                    (cells of up to ~230 particles); 0: recompute row i at every event.
                                    Both give bit-identical results (default 1) */
+#define MCD_OPT_TRACER 11       /* 1: every swarm carries the tracer column (mcd_get_tracer); 0 (default)
+                                   clears it.  mcd_set_tracer switches it on. */
 
 /*
  * Bytes of device workspace needed for n_disks disks at precision prec.
@@ -162,6 +164,22 @@ int mcd_regrid(mcd_ctx *ctx);
 
 /* One step: regrid, collide to t + dt, transport dt (dt > 0). */
 int mcd_step(mcd_ctx *ctx, double dt);
+
+/*
+ * A tracked property per swarm (SURVEY's extra tracked properties, e.g. a
+ * composition fraction), carried by the representative particle through the
+ * regrid and updated at every collision (a reading: the paper names no rule):
+ * sticking mixes by mass, (m_i q_i + g q_j) / (m_i + g) with g the absorbed
+ * mass; fragmentation gives the pair's mass-weighted mixture; erosion leaves the
+ * larger body's q and makes the smaller one debris of itself and erosion_chi
+ * times its mass chipped from the other, (q_i + chi q_j) / (1 + chi).  It starts
+ * at 0 and costs nothing while off.  q: disk `disk`'s n0 values in the order
+ * mcd_get_particles returns; where = MCD_HOST (synchronises) or MCD_DEVICE.
+ * mcd_set_tracer switches the tracer on; mcd_set_particles leaves the column
+ * as it is, slot by slot.
+ */
+int mcd_get_tracer(mcd_ctx *ctx, int32_t disk, double *q, int32_t where);
+int mcd_set_tracer(mcd_ctx *ctx, int32_t disk, const double *q, int32_t where);
 
 /*
  * Copy disk `disk`'s particles in cell order (dead ones, r = +inf, last).

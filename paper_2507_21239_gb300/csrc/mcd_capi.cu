@@ -94,6 +94,7 @@ size_t carve(mcd_ctx *c, void *base, const Sizes &S, int32_t nd)
         x->id[b] = cv.take<uint32_t>(S.N);
         x->key[b] = cv.take<uint64_t>(S.N);
         x->val[b] = cv.take<uint32_t>(S.N);
+        x->q[b] = cv.take<double>(S.N);
     }
     int64_t H = 256 * S.T;
     x->hist = cv.take<uint32_t>(H);
@@ -256,6 +257,8 @@ int mcd_init_disk(mcd_ctx **out, const mcd_disk_params *p, const mcd_grid *g, in
     if (e == cudaSuccess) e = cudaMemsetAsync(c->events_total, 0, 8 * n_disks, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->cell_events, 0, 8 * S.C, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->log_n, 0, 8, st);
+    for (int b = 0; b < 2; ++b)  // the tracer starts at zero (uniform: its order does not matter)
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->q[b], 0, 8 * S.N, st);
     if (e == cudaSuccess) e = prepare_collide(c);
     if (e == cudaSuccess) e = prepare_zone(c);
     if (e == cudaSuccess) e = launch_init(c, d_Mswarm);
@@ -389,6 +392,31 @@ int mcd_moments(mcd_ctx *c, int32_t disk, int32_t nbins, const double *edges, do
         e = cudaMemcpyAsync(out, c->diag_out, sizeof(double) * 5 * nbins, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     return cuda_code(e);
+}
+
+int mcd_get_tracer(mcd_ctx *c, int32_t disk, double *q, int32_t where)
+{
+    if (!c || disk < 0 || disk >= c->n_disks || !q || (where != MCD_HOST && where != MCD_DEVICE)) return MCD_EINVAL;
+    const DiskDev &D = c->hd[disk];
+    cudaError_t e = cudaMemcpyAsync(q, c->q[c->cur] + D.p_off, 8 * D.n0,
+                                    where == MCD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess && where == MCD_HOST) e = cudaStreamSynchronize(c->stream);
+    return cuda_code(e);
+}
+
+int mcd_set_tracer(mcd_ctx *c, int32_t disk, const double *q, int32_t where)
+{
+    if (!c || disk < 0 || disk >= c->n_disks || !q || (where != MCD_HOST && where != MCD_DEVICE)) return MCD_EINVAL;
+    const DiskDev &D = c->hd[disk];
+    cudaError_t e = cudaMemcpyAsync(c->q[c->cur] + D.p_off, q, 8 * D.n0,
+                                    where == MCD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess && where == MCD_HOST) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return MCD_ECUDA;
+    if (!c->tracer) {
+        c->tracer = 1;
+        drop_graphs(c);
+    }
+    return MCD_OK;
 }
 
 int mcd_sigma_map(mcd_ctx *c, int32_t disk, int32_t nr, const double *r_edges, int32_t nm, const double *m_edges,
@@ -605,6 +633,13 @@ int mcd_set_option(mcd_ctx *c, int32_t key, double v)
     case MCD_OPT_LOG_CELL: c->log_cell = (int64_t)v; break;
     case MCD_OPT_LPT: c->lpt = v != 0.0; break;
     case MCD_OPT_EXCLUSIVE: c->exclusive = v != 0.0; break;
+    case MCD_OPT_TRACER:
+        if (c->tracer && v == 0.0) {  // switched off: the column is cleared, not left stale
+            for (int b = 0; b < 2; ++b)
+                if (cudaMemsetAsync(c->q[b], 0, 8 * c->N, c->stream) != cudaSuccess) return MCD_ECUDA;
+        }
+        c->tracer = v != 0.0;
+        break;
     case MCD_OPT_DV_MATRIX: c->dv_matrix = v != 0.0; break;
     case MCD_OPT_THREADS:
         if (v != 0.0 && (v < c->n_max || v > kMaxCell || ((int)v % 32) != 0)) return MCD_EINVAL;

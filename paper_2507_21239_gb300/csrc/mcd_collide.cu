@@ -502,6 +502,21 @@ __device__ __forceinline__ double outcome_ramp(const CellK<T> &c, double mi, dou
     return outcome<T>(c, mi, mj, mih, mjh, dmmi, dv, u3, kind);
 }
 
+// The tracer of representative i after an event of the given kind: sticking
+// mixes by mass, (m_i q_i + g q_j) / m_new with g the absorbed mass;
+// fragmentation gives the pair's mass-weighted mixture; erosion leaves the
+// larger body's q and makes the smaller one debris of itself and chi times its
+// mass chipped from the other, (q_i + chi q_j) / (1 + chi).  FP64, explicitly
+// rounded (no fused multiply-add), like the plain CPU evaluation.
+__device__ __forceinline__ double tracer_update(double mi, double mj, double qi, double qj, double gain, double mnew,
+                                                int kind, double chi)
+{
+    if (kind == 0) return __ddiv_rn(__dadd_rn(__dmul_rn(mi, qi), __dmul_rn(gain, qj)), mnew);
+    if (kind == 1) return __ddiv_rn(__dadd_rn(__dmul_rn(mi, qi), __dmul_rn(mj, qj)), __dadd_rn(mi, mj));
+    if (!(mi < mj)) return qi;
+    return __ddiv_rn(__dadd_rn(qi, __dmul_rn(chi, qj)), __dadd_rn(1.0, chi));
+}
+
 // ---- accumulators: FP64 sum, or a compensated FP32 pair ------------------------
 template <class T>
 struct Acc;
@@ -590,6 +605,7 @@ struct CollideArgs {
     int64_t log_cap;
     int64_t n_cells;
     int dv_ld;  // row stride of the stored dv matrix (odd; STORE path)
+    double *q;  // the tracer column (TRACER variants)
 };
 
 template <class T>
@@ -621,7 +637,9 @@ __global__ void k_cellconst(const mcd_disk_params *params, const int32_t *cell_d
 // event is then read, not recomputed, and later full rebuilds sum stored
 // entries; pair_dv is symmetric bit for bit, so the results are those of the
 // recomputing path.
-template <class T, bool STORE, bool RAMP>
+// TRACER: the swarms carry a tracer column (shared-memory copy after the dv
+// row, before the matrix), updated on every event.
+template <class T, bool STORE, bool RAMP, bool TRACER>
 __global__ void __launch_bounds__(kMaxCell) k_collide(CollideArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -630,7 +648,8 @@ __global__ void __launch_bounds__(kMaxCell) k_collide(CollideArgs A)
     Part<T> *parts = reinterpret_cast<Part<T> *>(smem_raw);
     double *msh = reinterpret_cast<double *>(parts + nmax);
     T *dvrow = reinterpret_cast<T *>(msh + nmax);
-    T *Dm = dvrow + nmax;  // STORE: dv_kj at Dm[k * ld + j], an ld x ld block
+    double *qsh = reinterpret_cast<double *>(dvrow + nmax);  // TRACER
+    T *Dm = TRACER ? reinterpret_cast<T *>(qsh + nmax) : dvrow + nmax;  // STORE: dv_kj at Dm[k * ld + j], ld x ld
     const int ld = A.dv_ld;
 
     const int64_t cell = A.queue ? (int64_t)A.queue[blockIdx.x] : (int64_t)blockIdx.x;
@@ -663,6 +682,7 @@ __global__ void __launch_bounds__(kMaxCell) k_collide(CollideArgs A)
         // monomer mass and the disk's dust mass, inside the split's range
         if (sizeof(T) == 4 && !mass_splits(mk)) atomicOr(A.status, kStBadCell);
         msh[k] = mk;
+        if (TRACER) qsh[k] = A.q[off + k];
         pk = make_part<T>(c, mk, (T)(A.M[off + k] * c.invVsc));
         parts[k] = pk;
     }
@@ -794,6 +814,10 @@ __global__ void __launch_bounds__(kMaxCell) k_collide(CollideArgs A)
             const Part<T> pnew = make_part<T>(c, mnew, pi.Mv);
             const int stop = tn >= t_end;
             if (!stop) {
+                if constexpr (TRACER) {
+                    const double mj = msh[j];
+                    qsh[i] = tracer_update(mi, mj, qsh[i], qsh[j], dgt(dmmi, mj) ? dmmi : mj, mnew, kind, c.chi);
+                }
                 msh[i] = mnew;
                 parts[i] = pnew;
                 sh.t = tn;
@@ -838,6 +862,7 @@ __global__ void __launch_bounds__(kMaxCell) k_collide(CollideArgs A)
     }
     if (active) {
         A.m[off + k] = msh[k];
+        if (TRACER) A.q[off + k] = qsh[k];
         if (A.Rdump) A.Rdump[off + k] = R.value() / c.sc;
     }
     if (k == 0) {
@@ -969,6 +994,7 @@ static cudaError_t collide_impl(mcd_ctx *cx, int from_state, double t_end)
     A.queue = cx->lpt ? cx->queue : nullptr;
     A.m = cx->m[b];
     A.M = cx->M[b];
+    A.q = cx->tracer ? cx->q[b] : nullptr;
     A.cell_events = cx->cell_events;
     A.events_total = cx->events_total;
     A.state = cx->state;
@@ -993,33 +1019,53 @@ static cudaError_t collide_impl(mcd_ctx *cx, int from_state, double t_end)
     if (cx->exclusive && smem < kExclusiveSmem) smem = kExclusiveSmem;
     // FP32: the dv matrix (ld x ld, ld = n_max rounded up to odd) when it fits
     const int ld = cx->n_max | 1;
-    const size_t smem_store = collide_smem<T>(nthr) + (size_t)ld * ld * sizeof(T);
+    const size_t smem_store = collide_smem<T>(nthr) + (size_t)ld * ld * sizeof(T) +
+                              (cx->tracer ? (size_t)nthr * sizeof(double) : 0);
     const bool store = sizeof(T) == 4 && cx->dv_matrix && smem_store <= (size_t)cx->smem_optin;
     A.dv_ld = ld;
-    // a fragmentation ramp in any disk selects the kernel variant with its branch
+    // a fragmentation ramp in any disk, or the tracer, selects the kernel variant with its branch
     auto go = [&](auto kernel, size_t bytes) {
         kernel<<<(unsigned)cx->C, nthr, bytes, cx->stream>>>(A);
         cx->launches += 2;
         return cudaGetLastError();
     };
+    const size_t tq = cx->tracer ? (size_t)nthr * sizeof(double) : 0;  // the tracer's shared-memory copy
     if constexpr (sizeof(T) == 4)
         if (store) {
-            const size_t b = smem_store > smem ? smem_store : smem;
-            return cx->ramp ? go(k_collide<T, true, true>, b) : go(k_collide<T, true, false>, b);
+            const size_t b = smem_store > smem + tq ? smem_store : smem + tq;
+            if (cx->tracer)
+                return cx->ramp ? go(k_collide<T, true, true, true>, b) : go(k_collide<T, true, false, true>, b);
+            return cx->ramp ? go(k_collide<T, true, true, false>, b) : go(k_collide<T, true, false, false>, b);
         }
-    return cx->ramp ? go(k_collide<T, false, true>, smem) : go(k_collide<T, false, false>, smem);
+    if (cx->tracer)
+        return cx->ramp ? go(k_collide<T, false, true, true>, smem + tq) : go(k_collide<T, false, false, true>, smem + tq);
+    return cx->ramp ? go(k_collide<T, false, true, false>, smem) : go(k_collide<T, false, false, false>, smem);
 }
 
 // the dynamic shared memory each variant may request; for the stored-matrix
 // variant, what the device lets a block opt in to beyond its static part
+// the dynamic shared memory each variant may request; for the stored-matrix
+// variants, what the device lets a block opt in to beyond its static part
+template <class T, bool STORE>
+static cudaError_t set_smem(int bytes)
+{
+    cudaError_t e = cudaSuccess;
+    auto one = [&](auto kernel) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    };
+    one(k_collide<T, STORE, false, false>);
+    one(k_collide<T, STORE, true, false>);
+    one(k_collide<T, STORE, false, true>);
+    one(k_collide<T, STORE, true, true>);
+    return e;
+}
+
 template <class T>
 static cudaError_t prepare_impl(mcd_ctx *c)
 {
-    size_t need = collide_smem<T>(kMaxCell);
-    const int want = (int)(need > kExclusiveSmem ? need : kExclusiveSmem);
-    cudaError_t e = cudaFuncSetAttribute(k_collide<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_collide<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+    const size_t need = collide_smem<T>(kMaxCell);
+    cudaError_t e = set_smem<T, false>((int)((need > kExclusiveSmem ? need : kExclusiveSmem) +
+                                             (size_t)kMaxCell * sizeof(double)));  // + the tracer's copy
     c->smem_optin = 0;
     if constexpr (sizeof(T) != 4) {
         return e;
@@ -1029,15 +1075,20 @@ static cudaError_t prepare_impl(mcd_ctx *c)
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
             return e;
-        cudaFuncAttributes fa, fr;
-        if ((e = cudaFuncGetAttributes(&fa, k_collide<T, true, false>)) != cudaSuccess) return e;
-        if ((e = cudaFuncGetAttributes(&fr, k_collide<T, true, true>)) != cudaSuccess) return e;
-        const int st = (int)(fa.sharedSizeBytes > fr.sharedSizeBytes ? fa.sharedSizeBytes : fr.sharedSizeBytes);
+        int st = 0;
+        auto stat = [&](auto kernel) {
+            cudaFuncAttributes fa;
+            if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+            if (e == cudaSuccess && (int)fa.sharedSizeBytes > st) st = (int)fa.sharedSizeBytes;
+        };
+        stat(k_collide<T, true, false, false>);
+        stat(k_collide<T, true, true, false>);
+        stat(k_collide<T, true, false, true>);
+        stat(k_collide<T, true, true, true>);
+        if (e != cudaSuccess) return e;
         const int dyn = optin - st;
         if (dyn <= 0) return cudaSuccess;
-        e = cudaFuncSetAttribute(k_collide<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_collide<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        e = set_smem<T, true>(dyn);
         if (e == cudaSuccess) c->smem_optin = dyn;
         return e;
     }

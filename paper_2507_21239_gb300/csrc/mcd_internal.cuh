@@ -207,6 +207,7 @@ struct mcd_ctx {
     int32_t *status = nullptr;
     mcd::StepState *state = nullptr;
     double *d_Mswarm = nullptr;  // per-disk initial swarm mass
+    double *q[2] = {nullptr, nullptr};  // tracer column, double-buffered like the particle columns
     double *diag_edges = nullptr, *diag_out = nullptr;  // diagnostics: bin edges, per-bin sums
     unsigned long long *map_acc = nullptr;  // sigma map: per-bin unit counts, then the unit's exponent
     double *map_redges = nullptr, *map_medges = nullptr, *map_out = nullptr;
@@ -219,6 +220,7 @@ struct mcd_ctx {
     int32_t use_graph = 1, dump_R = 0, lpt = 1, threads = 0, exclusive = 1, dv_matrix = 1;
     int32_t smem_optin = 0;  // dynamic shared memory the stored-dv collide variant may request
     int32_t ramp = 0;        // some disk has a fragmentation ramp (frag_ramp > 0)
+    int32_t tracer = 0;      // the swarms carry the tracer column (MCD_OPT_TRACER / mcd_set_tracer)
     int64_t log_cell = -1;
 
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};

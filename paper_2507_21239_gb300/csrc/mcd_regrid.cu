@@ -390,6 +390,8 @@ struct ZoneArgs {
     const uint32_t *id0;
     double *m1, *M1, *r1, *z1;
     uint32_t *id1;
+    const double *q0;  // the tracer column, or null
+    double *q1;
     int64_t *cell_start;
     int32_t *cell_n;
     double *cell_b, *cell_V;
@@ -555,6 +557,7 @@ __global__ void __launch_bounds__(kZoneThreads, 2) k_zone(ZoneArgs A)
         A.r1[gd] = A.r0[gs];
         A.z1[gd] = key_value(el_key(e));
         A.id1[gd] = e.z;
+        if (A.q0) A.q1[gd] = A.q0[gs];
     }
 }
 
@@ -562,7 +565,7 @@ __global__ void __launch_bounds__(kZoneThreads, 2) k_zone(ZoneArgs A)
 __global__ void k_dead_tail(const DiskDev *disks, const int32_t *slot_disk, int64_t N, const int64_t *n_alive,
                             const uint32_t *rsrc, const double *m0, const double *M0, const double *r0,
                             const double *z0, const uint32_t *id0, double *m1, double *M1, double *r1, double *z1,
-                            uint32_t *id1)
+                            uint32_t *id1, const double *q0, double *q1)
 {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= N) return;
@@ -575,6 +578,7 @@ __global__ void k_dead_tail(const DiskDev *disks, const int32_t *slot_disk, int6
     r1[s] = r0[gs];
     z1[s] = z0[gs];
     id1[s] = id0[gs];
+    if (q0) q1[s] = q0[gs];
 }
 
 // the zone sort: the largest zone's size, the path (radix when the zone fits
@@ -639,6 +643,8 @@ cudaError_t launch_regrid(mcd_ctx *c)
     A.rsrc = c->val[0];
     A.m0 = c->m[b]; A.M0 = c->M[b]; A.r0 = c->r[b]; A.z0 = c->z[b]; A.id0 = c->id[b];
     A.m1 = c->m[nb]; A.M1 = c->M[nb]; A.r1 = c->r[nb]; A.z1 = c->z[nb]; A.id1 = c->id[nb];
+    A.q0 = c->tracer ? c->q[b] : nullptr;
+    A.q1 = c->tracer ? c->q[nb] : nullptr;
     A.cell_start = c->cell_start;
     A.cell_n = c->cell_n;
     A.cell_b = c->cell_b;
@@ -650,7 +656,8 @@ cudaError_t launch_regrid(mcd_ctx *c)
     A.id_passes = zp.id_passes;
     k_zone<<<(unsigned)c->Z, kZoneThreads, zp.smem, st>>>(A);
     k_dead_tail<<<gN, 256, 0, st>>>(c->d_disks, c->slot_disk, c->N, c->n_alive, c->val[0], c->m[b], c->M[b], c->r[b],
-                                    c->z[b], c->id[b], c->m[nb], c->M[nb], c->r[nb], c->z[nb], c->id[nb]);
+                                    c->z[b], c->id[b], c->m[nb], c->M[nb], c->r[nb], c->z[nb], c->id[nb],
+                                    c->tracer ? c->q[b] : nullptr, c->tracer ? c->q[nb] : nullptr);
     c->launches += 4 + 4 * kRadixPasses;
     return cudaGetLastError();
 }

@@ -18,7 +18,7 @@ MCD_OK, MCD_EINVAL, MCD_ENOMEM, MCD_ECUDA, MCD_ENAN, MCD_ETIMEOUT, MCD_EEMPTY, M
 MCD_FP64, MCD_MIXED = 0, 1
 MCD_HOST, MCD_DEVICE = 0, 1
 (MCD_OPT_MAX_EVENTS, MCD_OPT_CAP_STOPS, MCD_OPT_REBUILD_EVERY, MCD_OPT_USE_GRAPH, MCD_OPT_DUMP_R,
- MCD_OPT_LOG_CELL, MCD_OPT_LPT, MCD_OPT_THREADS, MCD_OPT_EXCLUSIVE, MCD_OPT_DV_MATRIX) = range(1, 11)
+ MCD_OPT_LOG_CELL, MCD_OPT_LPT, MCD_OPT_THREADS, MCD_OPT_EXCLUSIVE, MCD_OPT_DV_MATRIX, MCD_OPT_TRACER) = range(1, 12)
 PREC = {"fp64": MCD_FP64, "mixed": MCD_MIXED}
 
 
@@ -80,6 +80,8 @@ def lib():
         L.mcd_get_cell_events.argtypes = [_vp, C.c_int32, _vp, C.c_int32]
         L.mcd_get_event_log.argtypes = [_vp, _vp, _vp, _vp, C.c_int64, _P(C.c_int64)]
         L.mcd_get_stats.argtypes = [_vp, C.c_int32, _P(mcd_stats)]
+        L.mcd_get_tracer.argtypes = [_vp, C.c_int32, _vp, C.c_int32]
+        L.mcd_set_tracer.argtypes = [_vp, C.c_int32, _vp, C.c_int32]
         L.mcd_moments.argtypes = [_vp, C.c_int32, C.c_int32, _vp, _vp]
         L.mcd_sigma_map.argtypes = [_vp, C.c_int32, C.c_int32, _vp, C.c_int32, _vp, _vp]
         L.mcd_set_option.argtypes = [_vp, C.c_int32, C.c_double]
@@ -232,6 +234,14 @@ def mcd_sigma_map(ctx: int, disk: int, r_edges, m_edges) -> np.ndarray:
     return out
 
 
+def mcd_get_tracer(ctx: int, disk: int, q, where: int = MCD_HOST):
+    _check(lib().mcd_get_tracer(ctx, disk, _ptr(q), where), "mcd_get_tracer")
+
+
+def mcd_set_tracer(ctx: int, disk: int, q, where: int = MCD_HOST):
+    _check(lib().mcd_set_tracer(ctx, disk, _ptr(q), where), "mcd_set_tracer")
+
+
 def mcd_set_option(ctx: int, key: int, value: float):
     _check(lib().mcd_set_option(ctx, key, float(value)), "mcd_set_option")
 
@@ -314,6 +324,15 @@ class Disk:
 
     def stats(self, disk: int = 0) -> mcd_stats:
         return mcd_get_stats(self.ctx, disk)
+
+    def tracer(self, disk: int = 0) -> np.ndarray:
+        g = self.grids[disk] if isinstance(self.grids[0], (tuple, list)) else self.grids
+        q = np.zeros(int(g[0]) * int(g[1]) * int(g[2]))
+        mcd_get_tracer(self.ctx, disk, q)
+        return q
+
+    def set_tracer(self, q, disk: int = 0):
+        mcd_set_tracer(self.ctx, disk, np.ascontiguousarray(q, dtype=np.float64))
 
     def moments(self, edges, disk: int = 0) -> np.ndarray:
         return mcd_moments(self.ctx, disk, edges)

@@ -533,3 +533,74 @@ def test_sigma_map_matches_oracle(prec):
     with pytest.raises(mcd.McdError):
         d.sigma_map(r_edges, np.geomspace(1e-12, 1e6, 5000))
     d.close()
+
+
+# ------------------------------------------------------------------- tracer ---
+def test_tracer_event_chain_fp64_matches_oracle():
+    """FP64, same keys: one cell's event chain leaves the tracer column the
+    oracle's, for a chain with sticking, fragmentation and erosion."""
+    P = W.benchmark_disk(v_frag=30.0, dm_group=1e-3)
+    n = 60
+    masses = W.random_masses(n, seed=9, lo=1e-6, hi=1e-2)
+    d, cell, b, V = _one_cell(P, n, 21, mcd.MCD_FP64, masses)
+    q0 = np.random.default_rng(4).uniform(0.1, 0.9, n)
+    d.set_tracer(q0)
+    R = oracle.rate_matrix(P, b[4], b[5], V, cell["m"], cell["M"])[1]
+    t_end = 3000.0 / R.sum()
+    mcd.mcd_collide(d.ctx, t_end)
+    assert mcd.mcd_sync(d.ctx) == mcd.MCD_OK
+    st, m_o, q_o, ev_o, _, _ = oracle.collide_cell_q(P, b[4], b[5], V, cell["m"], cell["M"], q0, 0.0, t_end, 21, 0,
+                                                     0, 0)
+    assert ev_o > 1000 and d.stats().events == ev_o
+    assert rel(d.particles()["m"], m_o) < 1e-12
+    assert rel(d.tracer(), q_o) < 1e-12
+    d.close()
+
+
+def test_tracer_steps_fp64_match_oracle():
+    """Three full FP64 steps with the tracer a function of the id on both
+    sides: every particle's tracer equals the oracle's."""
+    P = W.benchmark_disk(dust_to_gas=0.5, v_frag=300.0)
+    grid, seed, dt = (6, 3, 20), 4, 100 * YR
+    d = _make_ctx(P, grid, seed=seed)
+    f = lambda ids: 0.1 + 0.8 * (ids.astype(float) % 7) / 6.0
+    d.set_tracer(f(d.particles()["id"]))
+    s = oracle.init_disk(P, 6 * 3 * 20, seed)
+    s.q = f(s.id)
+    for _ in range(3):
+        d.step(dt)
+    assert mcd.mcd_sync(d.ctx) == mcd.MCD_OK
+    oracle.run(P, 6, 3, s, 0.0, dt, 0, 3, seed)
+    got, q = d.particles(), d.tracer()
+    go, so = np.argsort(got["id"]), np.argsort(s.id)
+    assert mcd.mcd_get_stats(d.ctx, 0).events == s.events > 100_000
+    assert rel(q[go], s.q[so]) < 1e-10
+    assert not np.array_equal(q[go], f(got["id"][go]))  # the tracer did change
+    d.close()
+
+
+def test_tracer_mixed_invariants_regrid_and_switch_off():
+    """Mixed path: a uniform tracer stays uniform and a spread one stays in its
+    range over full steps; the tracer follows its particle through a regrid;
+    get/set round trip; switching the tracer off clears it."""
+    P = W.benchmark_disk(dust_to_gas=0.3)
+    d = _make_ctx(P, (8, 4, 30), seed=2, prec=mcd.MCD_MIXED)
+    d.set_tracer(np.full(8 * 4 * 30, 0.25))
+    for _ in range(3):
+        d.step(40 * YR)
+    assert mcd.mcd_sync(d.ctx) == mcd.MCD_OK and d.stats().events > 1000
+    assert np.allclose(d.tracer(), 0.25, rtol=1e-14, atol=0)
+    ids = d.particles()["id"]
+    q0 = 0.2 + 0.6 * (ids % 11) / 10.0
+    d.set_tracer(q0)
+    assert np.array_equal(d.tracer(), q0)
+    mcd.mcd_regrid(d.ctx)
+    x = d.particles()
+    assert np.array_equal(d.tracer(), 0.2 + 0.6 * (x["id"] % 11) / 10.0)
+    for _ in range(3):
+        d.step(40 * YR)
+    q = d.tracer()
+    assert q.min() >= 0.2 * (1 - 1e-12) and q.max() <= 0.8 * (1 + 1e-12)
+    mcd.mcd_set_option(d.ctx, mcd.MCD_OPT_TRACER, 0)
+    assert np.array_equal(d.tracer(), np.zeros_like(q))
+    d.close()
