@@ -47,15 +47,27 @@ class Params(C.Structure):
         "dust_to_gas", "r_in", "r_out", "m_star", "rho_s", "a_mono",
         "mu", "sigma_h2", "dm_group", "frag_xi", "erosion_chi",
         "K_const", "V_const", "m_init", "M_total", "frag_ramp")] + [
-        (n, C.c_int32) for n in ("kernel_mode", "settle_form", "dv_flags", "tr_flags")]
+        (n, C.c_int32) for n in ("kernel_mode", "settle_form", "dv_flags", "tr_flags")] + [
+        ("gas_tab", C.c_void_p), ("gas_n", C.c_int32)]
 
     OPTIONAL = {"frag_ramp": 0.0}  # keys a caller's dict may leave out
 
     @classmethod
     def from_dict(cls, d: dict) -> "Params":
+        """d may hold "gas_table": rows (r, Sigma_g, T) of a tabulated gas disk."""
         p = cls()
         for name, _ in cls._fields_:
+            if name in ("gas_tab", "gas_n"):
+                continue
             setattr(p, name, d[name] if name in d or name not in cls.OPTIONAL else cls.OPTIONAL[name])
+        tab = d.get("gas_table")
+        if tab is not None:
+            t = np.ascontiguousarray(tab, dtype=np.float64).reshape(-1, 3)
+            p._tab = t  # kept alive with the structure
+            p.gas_tab = t.ctypes.data
+            p.gas_n = t.shape[0]
+        else:
+            p.gas_tab, p.gas_n = None, 0
         return p
 
 

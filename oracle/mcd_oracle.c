@@ -5,7 +5,7 @@
  * coagulation step of mcdust (Vaikundaraman, Gurrutxaga & Drazkowska 2025,
  * "mcdust: A 2D Monte Carlo code for dust coagulation in protoplanetary
  * disks", Summary section): a static, vertically isothermal power-law gas disk
- * (Benchmark table), swarms of identical particles followed through one
+ * (Benchmark table) or one tabulated in radius, swarms of identical particles followed through one
  * representative each (Zsom & Dullemond 2008, cited in the Summary), sticking,
  * fragmentation and erosion outcomes (Summary), radial and vertical transport
  * (Summary), and an adaptive grid whose cells hold equal numbers of
@@ -84,6 +84,10 @@ typedef struct {
     int32_t settle_form; /* 0: v_z = -z Omega St ; 1: -z Omega St/(1+St) */
     int32_t dv_flags;    /* ORC_DV_* mask */
     int32_t tr_flags;    /* ORC_TR_* mask */
+    /* a tabulated (non-power-law) gas disk, reading: gas_n knots r_k, Sigma_k,
+       T_k at gas_tab[3k .. 3k+2], r_k increasing; 0 knots: the power laws */
+    const double *gas_tab;
+    int32_t gas_n;
 } orc_params;
 
 /* ======================================================================== */
@@ -132,14 +136,58 @@ static void orc_draw(uint64_t seed, uint64_t disk, uint64_t c0, uint64_t c1, uin
 /* ======================================================================== */
 typedef struct {
     double Sigma, T, cs, Omega, H, rho, vth, lambda, nu, etavk, D, vg2, St_eta, asw;
+    double p, q; /* local slopes -dln Sigma/dln r, -dln T/dln r */
 } orc_gas;
+
+/* Knot k's ln Sigma, ln T and the slopes p_k = -(ln Sigma_{k+1} - ln Sigma_k) /
+ * (ln r_{k+1} - ln r_k), q_k likewise, of segment [r_k, r_{k+1}) (the last
+ * segment's slopes are repeated at the last knot).  Between knots Sigma and T
+ * are linear in log-log: Sigma(r) = exp(ln Sigma_k - p_k (ln r - ln r_k)) with
+ * k the last knot not above r (the first below r_0); beyond the ends the end
+ * segments extend.  A power law is therefore reproduced exactly. */
+void orc_gas_table_prep(int32_t n, const double *tab, double *lnr, double *lnS, double *lnT, double *ps, double *qs)
+{
+    for (int32_t k = 0; k < n; ++k) {
+        lnr[k] = log(tab[3 * k]);
+        lnS[k] = log(tab[3 * k + 1]);
+        lnT[k] = log(tab[3 * k + 2]);
+    }
+    for (int32_t k = 0; k + 1 < n; ++k) {
+        const double dl = lnr[k + 1] - lnr[k];
+        ps[k] = -(lnS[k + 1] - lnS[k]) / dl;
+        qs[k] = -(lnT[k + 1] - lnT[k]) / dl;
+    }
+    ps[n - 1] = ps[n - 2];
+    qs[n - 1] = qs[n - 2];
+}
+
+/* Sigma, T and the local slopes at r from the table */
+static void orc_gas_table(const orc_params *P, double r, double *Sigma, double *T, double *p, double *q)
+{
+    const int32_t n = P->gas_n;
+    double lnr[n], lnS[n], lnT[n], ps[n], qs[n];
+    orc_gas_table_prep(n, P->gas_tab, lnr, lnS, lnT, ps, qs);
+    int32_t k = 0;
+    while (k + 2 < n && P->gas_tab[3 * (k + 1)] <= r) ++k; /* segment [r_k, r_k+1), ends extended */
+    const double dl = log(r) - lnr[k];
+    *Sigma = exp(lnS[k] - ps[k] * dl);
+    *T = exp(lnT[k] - qs[k] * dl);
+    *p = ps[k];
+    *q = qs[k];
+}
 
 static orc_gas orc_gas_at(const orc_params *P, double r, double z)
 {
     orc_gas g;
-    double x = r / ORC_AU;
-    g.Sigma = P->sigma0 * pow(x, -P->p);
-    g.T = P->T0 * pow(x, -P->q);
+    if (P->gas_n >= 2) {
+        orc_gas_table(P, r, &g.Sigma, &g.T, &g.p, &g.q);
+    } else {
+        double x = r / ORC_AU;
+        g.Sigma = P->sigma0 * pow(x, -P->p);
+        g.T = P->T0 * pow(x, -P->q);
+        g.p = P->p;
+        g.q = P->q;
+    }
     g.cs = sqrt(ORC_KB * g.T / (P->mu * ORC_MP));
     g.Omega = sqrt(P->m_star * ORC_GM_SUN / (r * r * r));
     g.H = g.cs / g.Omega;
@@ -150,7 +198,7 @@ static orc_gas orc_gas_at(const orc_params *P, double r, double z)
     g.nu = 0.5 * g.vth * g.lambda;
     /* eta v_K = -(1/2) c_s^2/(Omega r) dlnP/dlnr with the midplane pressure
        P ~ r^-(p + (3+q)/2) (reading: midplane gradient at every height). */
-    g.etavk = 0.5 * g.cs * g.cs / (g.Omega * r) * (P->p + 0.5 * (3.0 + P->q));
+    g.etavk = 0.5 * g.cs * g.cs / (g.Omega * r) * (g.p + 0.5 * (3.0 + g.q));
     g.D = P->alpha * g.cs * g.H;              /* Schmidt number 1 (reading) */
     g.vg2 = 1.5 * P->alpha * g.cs * g.cs;     /* Ormel & Cuzzi V_g^2 (reading) */
     g.St_eta = 1.0 / sqrt(g.D / g.nu);        /* Re^-1/2, Re = alpha c_s H / nu */
@@ -731,7 +779,7 @@ static void orc_transport_one(const orc_params *P, double *r, double *z, double 
     if (P->tr_flags & ORC_TR_RADIAL) {
         double vr = -2.0 * g.etavk * St / (1.0 + St * St);
         /* (1/(r rho_g)) d/dr (r D rho_g) for D ~ r^(3/2-q), rho_g(r, z) */
-        double vD = g.D / r0 * (1.0 - P->p - 0.5 * P->q + z0 * z0 / (g.H * g.H) * 0.5 * (3.0 - P->q));
+        double vD = g.D / r0 * (1.0 - g.p - 0.5 * g.q + z0 * z0 / (g.H * g.H) * 0.5 * (3.0 - g.q));
         rn = r0 + (vr + vD) * dt + sqrt(2.0 * g.D * dt) * xi1;
     }
     if (P->tr_flags & ORC_TR_VERTICAL) {

@@ -712,3 +712,102 @@ def test_tracer_follows_its_particle_through_regrid():
     s.q = s.id.astype(float) / N
     st = oracle.regrid(P0, 5, 3, s)[0]
     assert st == 0 and np.array_equal(s.q, s.id.astype(float) / N)
+
+
+# ---- a gas disk tabulated in radius ------------------------------------------
+def _bump_table(n=48):
+    """Knots (r, Sigma_g, T) of a power-law disk with a Gaussian pressure bump
+    at 20 AU and a temperature break at 10 AU."""
+    rk = AU * np.geomspace(1.0, 300.0, n)
+    x = rk / AU
+    S = P0["sigma0"] * x**-1.0 * (1 + 3.0 * np.exp(-((x - 20.0) ** 2) / (2 * 2.0**2)))
+    T = np.where(x < 10.0, 280.0 * x**-0.5, 280.0 * 10.0**-0.5 * (x / 10.0) ** -0.75)
+    return np.c_[rk, S, T]
+
+
+def test_gas_table_of_a_power_law_reproduces_the_power_law():
+    """Knots sampled from the analytic Sigma_g, T give back every gas field, at
+    knots, between them and beyond both ends (log-log interpolation and
+    end-segment extension are exact on a power law)."""
+    rk = AU * np.geomspace(0.7, 150, 9)
+    tab = np.c_[rk, P0["sigma0"] * (rk / AU) ** -P0["p"], P0["T0"] * (rk / AU) ** -P0["q"]]
+    r = AU * np.geomspace(0.3, 300, 41)
+    for zH in (0.0, 1.5):
+        z = zH * oracle.gas(P0, r, 0.0)["H"]
+        g0, g1 = oracle.gas(P0, r, z), oracle.gas(dict(P0, gas_table=tab), r, z)
+        for k in g0:
+            assert np.max(np.abs(g1[k] / g0[k] - 1)) < 1e-13, k
+
+
+def test_gas_table_log_log_interpolation():
+    """Sigma_g and T between knots equal numpy's linear interpolation of
+    (ln r, ln Sigma), (ln r, ln T); at the knots the knot values; beyond the
+    ends the first and last segments continue."""
+    tab = _bump_table()
+    Pt = dict(P0, gas_table=tab)
+    lr, lS, lT = np.log(tab[:, 0]), np.log(tab[:, 1]), np.log(tab[:, 2])
+    r = AU * np.geomspace(1.0, 300.0, 997)
+    r[-1] = tab[-1, 0]
+    g = oracle.gas(Pt, r, 0.0)
+    assert np.max(np.abs(g["Sigma"] / np.exp(np.interp(np.log(r), lr, lS)) - 1)) < 1e-12
+    assert np.max(np.abs(g["T"] / np.exp(np.interp(np.log(r), lr, lT)) - 1)) < 1e-12
+    gk = oracle.gas(Pt, tab[:, 0], 0.0)
+    assert np.max(np.abs(gk["Sigma"] / tab[:, 1] - 1)) < 1e-13
+    assert np.max(np.abs(gk["T"] / tab[:, 2] - 1)) < 1e-13
+    for rr, a, b in ((0.5 * AU, 0, 1), (400 * AU, -2, -1)):
+        s = (lS[b] - lS[a]) / (lr[b] - lr[a])
+        ref = np.exp(lS[a] + s * (np.log(rr) - lr[a]))
+        assert abs(oracle.gas(Pt, rr, 0.0)["Sigma"][0] / ref - 1) < 1e-12
+
+
+def _mid_segment(tab, r_au):
+    """The midpoint (in ln r) of the table segment holding r_au AU."""
+    k = np.searchsorted(tab[:, 0], r_au * AU, side="right") - 1
+    return np.sqrt(tab[k, 0] * tab[k + 1, 0])
+
+
+@pytest.mark.parametrize("r_au", [3.0, 17.0, 21.0, 60.0])
+def test_gas_table_pressure_gradient_speed(r_au):
+    """eta v_K from the table's local slopes equals -(1/2) c_s^2/(Omega r)
+    dlnP/dlnr with the derivative of the tabulated midplane pressure taken
+    numerically inside a segment; on the inner flank of the bump (17 AU) the
+    pressure rises outward and eta v_K changes sign."""
+    tab = _bump_table()
+    Pt = dict(P0, gas_table=tab)
+    r = _mid_segment(tab, r_au)
+    g = oracle.gas(Pt, r, 0.0)
+    ref = -0.5 * g["cs"][0] ** 2 / (g["Omega"][0] * r) * _dlnP_dlnr(Pt, r)
+    assert abs(g["etavk"][0] / ref - 1) < 1e-6
+    assert (g["etavk"][0] < 0) == (r_au == 17.0)
+
+
+@pytest.mark.parametrize("zH", [0.0, 2.0])
+def test_gas_table_radial_step_mean(zH):
+    """One Ito step in a tabulated disk, on the inner flank of the pressure
+    bump where the local slopes are far from the outer power law:
+    E[dr] = (v_r + (1/(r rho)) d(r D rho)/dr) dt with the derivative and
+    dlnP/dlnr taken numerically from the tabulated gas."""
+    tab = _bump_table()
+    Pt = dict(P0, gas_table=tab, tr_flags=W.TR_RADIAL)
+    r = _mid_segment(tab, 17.0)
+    g = oracle.gas(Pt, r, 0.0)
+    z = zH * g["H"][0]
+    n = 1_000_000
+    s = _monomer_at(Pt, r, z, n)
+    dt = 3e4 * YR
+    oracle.transport(Pt, s, dt, seed=5, disk=0, step=0)
+    dr = s.r - r
+
+    def f(x):
+        gg = oracle.gas(Pt, x, z)
+        return x * gg["D"][0] * gg["rho"][0]
+    h = 1e-5 * r
+    gz = oracle.gas(Pt, r, z)
+    vD = (f(r + h) - f(r - h)) / (2 * h) / (r * gz["rho"][0])
+    a = Pt["a_mono"]
+    St = np.pi * a * Pt["rho_s"] / (2 * g["Sigma"][0]) * np.exp(z**2 / (2 * g["H"][0] ** 2))
+    etavk = -0.5 * g["cs"][0] ** 2 / (g["Omega"][0] * r) * _dlnP_dlnr(Pt, r)
+    vr = -2 * etavk * St / (1 + St**2)
+    se = np.sqrt(2 * gz["D"][0] * dt / n)
+    assert abs(dr.mean() - (vr + vD) * dt) < 5 * se
+    assert abs(vD * dt) > 15 * se
