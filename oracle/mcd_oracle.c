@@ -602,7 +602,8 @@ int orc_collide_cell_q(const orc_params *P, double rc, double zc, double V, int6
 
 /* ======================================================================== */
 /* Initial state (workload recipe): equal swarm masses, r drawn from the    */
-/* dust-mass CDF ~ r^(2-p), z ~ N(0, H_g(r)), monomers.                     */
+/* dust-mass CDF ~ r^(2-p), z ~ N(0, H_g(r)), monomers.  The draw follows   */
+/* the power-law disk even when a gas table is set (reading).              */
 /* ======================================================================== */
 double orc_disk_dust_mass(const orc_params *P)
 {
@@ -628,7 +629,9 @@ void orc_init_disk(const orc_params *P, int64_t N, uint64_t seed, uint64_t disk,
             rr = pow(lo + u[0] * (hi - lo), 1.0 / e);
         }
         double xi = sqrt(-2.0 * log(u[1])) * cos(2.0 * ORC_PI * u[2]);
-        orc_gas g = orc_gas_at(P, rr, 0.0);
+        orc_params Pw = *P;
+        Pw.gas_n = 0;
+        orc_gas g = orc_gas_at(&Pw, rr, 0.0);
         r[k] = rr;
         z[k] = g.H * xi;
         m[k] = m0;

@@ -483,6 +483,10 @@ def test_init_disk_distributions():
     assert stats.kstest(s.z / H, "norm").pvalue > 1e-3
     assert np.array_equal(np.sort(s.id), np.arange(N, dtype=np.uint32))
     assert np.all(s.m == 4 / 3 * np.pi * P["rho_s"] * P["a_mono"] ** 3)
+    # the draw follows the power-law disk whatever gas table is set
+    t = oracle.init_disk(dict(P, gas_table=_bump_table()), N, seed=5, disk=2)
+    for k in ("m", "M", "r", "z", "id"):
+        assert np.array_equal(getattr(t, k), getattr(s, k)), k
 
 
 # ------------------------------------------------------------- bookkeeping ---
