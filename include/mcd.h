@@ -8,8 +8,9 @@
  * (mcd_regrid); in every cell, the representative-particle Monte Carlo
  * collision chain of Zsom & Dullemond (2008) with sticking, fragmentation and
  * erosion outcomes (mcd_collide); then radial and vertical transport of the
- * particles in a static, vertically isothermal power-law gas disk
- * (mcd_transport).  mcd_step runs the three in that order.
+ * particles in a static, vertically isothermal power-law gas disk, or one
+ * tabulated in radius (mcd_set_gas_table) (mcd_transport).  mcd_step runs the
+ * three in that order.
  *
  * Conventions for every call:
  *  - CGS units; times in seconds.
@@ -256,6 +257,25 @@ int mcd_moments(mcd_ctx *ctx, int32_t disk, int32_t nbins, const double *edges, 
 int mcd_sigma_map(mcd_ctx *ctx, int32_t disk, int32_t nr, const double *r_edges, int32_t nm, const double *m_edges,
                   double *out);
 int mcd_set_option(mcd_ctx *ctx, int32_t key, double value);
+
+/* A gas disk tabulated in radius in place of the power laws Sigma0 (r/AU)^-p,
+ * T0 (r/AU)^-q: the azimuthally averaged profile of a hydrodynamic snapshot
+ * that the method post-processes (Statement of Need section).  n knots r[k] [cm],
+ * Sigma[k] [g cm^-2], T[k] [K] (host arrays): r strictly increasing, every
+ * value finite and positive.  Between knots Sigma and T are linear in
+ * ln r - ln Sigma (ln T), and the first and last segments extend beyond the
+ * ends, so a table sampled from a power law gives that power law back; the
+ * pressure-gradient speed eta v_K and the radial diffusion drift take the
+ * logarithmic slopes of the segment holding r.  The disk stays vertically
+ * isothermal with a Gaussian profile.  n = 0 restores the power laws; n = 1,
+ * n > MCD_MAX_GAS_KNOTS or a bad value give MCD_EINVAL and leave the table
+ * as it was.  The table is read by every later collide, transport and regrid
+ * (a captured step graph stays valid); the initial draw of mcd_init_disk, the
+ * probes and mcd_regrid_noalloc use the power laws.  The host arrays may be
+ * released when the call returns (it synchronises the context's stream). */
+#define MCD_MAX_GAS_KNOTS 1024
+int mcd_set_gas_table(mcd_ctx *ctx, int32_t disk, int32_t n, const double *r, const double *Sigma,
+                      const double *T);
 
 /*
  * Phase tracing.  With on = 1 every later mcd_step records CUDA events on the

@@ -125,6 +125,8 @@ size_t carve(mcd_ctx *c, void *base, const Sizes &S, int32_t nd)
     x->map_redges = cv.take<double>(MCD_MAX_MAP_EDGES + 1);
     x->map_medges = cv.take<double>(MCD_MAX_MAP_EDGES + 1);
     x->map_out = cv.take<double>(MCD_MAX_MAP_BINS);
+    x->gas_knots = cv.take<GasKnot>((size_t)nd * kMaxGasKnots);
+    x->gas_n = cv.take<int32_t>(nd);
     return (cv.off + 255) & ~(size_t)255;
 }
 
@@ -218,6 +220,7 @@ int mcd_init_disk(mcd_ctx **out, const mcd_disk_params *p, const mcd_grid *g, in
     for (int32_t d = 0; d < n_disks; ++d)
         if (p[d].frag_ramp > 0.0) c->ramp = 1;
     c->hg.assign(g, g + n_disks);
+    c->gas_n_host.assign(n_disks, 0);
     c->hd = S.disks;
     c->N = S.N;
     c->C = S.C;
@@ -257,6 +260,7 @@ int mcd_init_disk(mcd_ctx **out, const mcd_disk_params *p, const mcd_grid *g, in
     if (e == cudaSuccess) e = cudaMemsetAsync(c->events_total, 0, 8 * n_disks, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->cell_events, 0, 8 * S.C, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->log_n, 0, 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->gas_n, 0, 4 * n_disks, st);  // the power laws
     for (int b = 0; b < 2; ++b)  // the tracer starts at zero (uniform: its order does not matter)
         if (e == cudaSuccess) e = cudaMemsetAsync(c->q[b], 0, 8 * S.N, st);
     if (e == cudaSuccess) e = prepare_collide(c);
@@ -416,6 +420,49 @@ int mcd_set_tracer(mcd_ctx *c, int32_t disk, const double *q, int32_t where)
         c->tracer = 1;
         drop_graphs(c);
     }
+    return MCD_OK;
+}
+
+int mcd_set_gas_table(mcd_ctx *c, int32_t disk, int32_t n, const double *r, const double *Sigma, const double *T)
+{
+    if (!c || disk < 0 || disk >= c->n_disks || n < 0 || n == 1 || n > kMaxGasKnots) return MCD_EINVAL;
+    if (n > 0 && (!r || !Sigma || !T)) return MCD_EINVAL;
+    std::vector<GasKnot> k((size_t)n);
+    for (int32_t i = 0; i < n; ++i) {
+        if (!(r[i] > 0.0 && r[i] < INFINITY) || !(Sigma[i] > 0.0 && Sigma[i] < INFINITY) ||
+            !(T[i] > 0.0 && T[i] < INFINITY) || (i > 0 && !(r[i] > r[i - 1])))
+            return MCD_EINVAL;
+        k[i].r = r[i];
+        k[i].S = Sigma[i];
+        k[i].T = T[i];
+        k[i].lnr = log(r[i]);
+        k[i].lnS = log(Sigma[i]);
+        k[i].lnT = log(T[i]);
+    }
+    // slopes of segment [r_i, r_i+1): -d ln Sigma / d ln r, -d ln T / d ln r
+    for (int32_t i = 0; i + 1 < n; ++i) {
+        const double dl = k[i + 1].lnr - k[i].lnr;
+        k[i].p = -(k[i + 1].lnS - k[i].lnS) / dl;
+        k[i].q = -(k[i + 1].lnT - k[i].lnT) / dl;
+    }
+    if (n > 0) {
+        k[n - 1].p = k[n - 2].p;
+        k[n - 1].q = k[n - 2].q;
+    }
+    cudaError_t e = cudaSuccess;
+    if (n > 0)
+        e = cudaMemcpyAsync(c->gas_knots + (int64_t)disk * kMaxGasKnots, k.data(), sizeof(GasKnot) * n,
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->gas_n + disk, &n, 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_code(e);
+    // transport has a variant that reads no table: a captured step graph is
+    // rebuilt when the first table comes or the last one goes
+    const int32_t before = c->gas_tables;
+    c->gas_n_host[disk] = n;
+    c->gas_tables = 0;
+    for (int32_t k : c->gas_n_host) c->gas_tables += k > 0;
+    if ((before > 0) != (c->gas_tables > 0)) drop_graphs(c);
     return MCD_OK;
 }
 

@@ -64,10 +64,10 @@ __device__ __forceinline__ void split(double x, T &h, T &l)
 }
 
 template <class T>
-__device__ CellK<T> make_cell(const mcd_disk_params &P, double rc, double zc, double V, double Mref)
+__device__ CellK<T> make_cell(const mcd_disk_params &P, GasTab tab, double rc, double zc, double V, double Mref)
 {
     CellK<T> c;
-    Gas<double> g = gas_at<double>(P, rc, zc);
+    Gas<double> g = gas_at<double>(P, tab, rc, zc);
     double Cep = P.rho_s / (g.rho * g.vth) * g.Omega;
     double Cst = 2.0 * P.rho_s / (9.0 * g.nu * g.rho) * g.Omega;
     double cm = 3.0 / (4.0 * kPI * P.rho_s);
@@ -621,15 +621,17 @@ struct Shared {
 // per-cell constants: one thread per cell, all SMs (the FP64 gas evaluation is
 // long; done here it leaves the collide CTAs' critical path)
 template <class T>
-__global__ void k_cellconst(const mcd_disk_params *params, const int32_t *cell_disk, const int64_t *cell_start,
-                            const int32_t *cell_n, const double *cell_b, const double *cell_V, const double *M,
-                            unsigned char *cellk, int64_t C)
+__global__ void k_cellconst(const mcd_disk_params *params, const GasKnot *gas_knots, const int32_t *gas_n,
+                            const int32_t *cell_disk, const int64_t *cell_start, const int32_t *cell_n,
+                            const double *cell_b, const double *cell_V, const double *M, unsigned char *cellk,
+                            int64_t C)
 {
     int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= C || cell_n[c] <= 0) return;
     const double *b = cell_b + 6 * c;
+    const int d = cell_disk[c];
     *reinterpret_cast<CellK<T> *>(cellk + c * kCellKBytes) =
-        make_cell<T>(params[cell_disk[c]], b[4], b[5], cell_V[c], M[cell_start[c]]);
+        make_cell<T>(params[d], gas_tab(gas_knots, gas_n, d), b[4], b[5], cell_V[c], M[cell_start[c]]);
 }
 
 // STORE (FP32 only): the cell's dv matrix lives in shared memory (row stride
@@ -878,7 +880,7 @@ __global__ void k_pair_probe(mcd_disk_params P, double rc, double zc, int64_t n,
                              const double *mj, double *dv, double *K)
 {
     __shared__ CellK<T> c;
-    if (threadIdx.x == 0) c = make_cell<T>(P, rc, zc, 1.0, 0.0);
+    if (threadIdx.x == 0) c = make_cell<T>(P, GasTab{nullptr, 0}, rc, zc, 1.0, 0.0);
     __syncthreads();
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
         Part<T> a = make_part<T>(c, mi[q], (T)0), b = make_part<T>(c, mj[q], (T)0);
@@ -896,7 +898,7 @@ __global__ void k_rate_probe(mcd_disk_params P, double rc, double zc, double V, 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Part<T> *parts = reinterpret_cast<Part<T> *>(smem_raw);
     __shared__ CellK<T> c;
-    if (threadIdx.x == 0) c = make_cell<T>(P, rc, zc, V, M[0]);
+    if (threadIdx.x == 0) c = make_cell<T>(P, GasTab{nullptr, 0}, rc, zc, V, M[0]);
     __syncthreads();
     for (int q = threadIdx.x; q < n; q += blockDim.x) parts[q] = make_part<T>(c, m[q], (T)(M[q] * c.invVsc));
     __syncthreads();
@@ -981,7 +983,8 @@ static cudaError_t collide_impl(mcd_ctx *cx, int from_state, double t_end)
     if (cx->C == 0) return cudaSuccess;
     const int b = cx->cur;
     k_cellconst<T><<<(unsigned)((cx->C + 127) / 128), 128, 0, cx->stream>>>(
-        cx->d_params, cx->cell_disk, cx->cell_start, cx->cell_n, cx->cell_b, cx->cell_V, cx->M[b], cx->cellk, cx->C);
+        cx->d_params, cx->gas_knots, cx->gas_n, cx->cell_disk, cx->cell_start, cx->cell_n, cx->cell_b, cx->cell_V,
+        cx->M[b], cx->cellk, cx->C);
     CollideArgs A;
     A.params = cx->d_params;
     A.disks = cx->d_disks;

@@ -88,7 +88,40 @@ __host__ __device__ inline float u01f(uint64_t x)
 template <class T>
 struct Gas {
     T Sigma, T_, cs, Omega, H, rho, vth, lambda, nu, etavk, D, vg2, St_eta, asw;
+    T p, q;  // local slopes -dln Sigma/dln r, -dln T/dln r
 };
+
+// A disk's gas table (mcd_set_gas_table), prepared on the host: knot k holds
+// r_k, ln r_k, ln Sigma_k, ln T_k, Sigma_k, T_k and the slopes p_k, q_k of
+// segment [r_k, r_{k+1}).  n < 2: the power laws.
+struct GasKnot {
+    double r, lnr, lnS, lnT, S, T, p, q;
+};
+struct GasTab {
+    const GasKnot *k;
+    int n;
+};
+constexpr int kMaxGasKnots = MCD_MAX_GAS_KNOTS;
+
+__device__ __forceinline__ GasTab gas_tab(const GasKnot *pool, const int32_t *gas_n, int d)
+{
+    return gas_n ? GasTab{pool + (int64_t)d * kMaxGasKnots, gas_n[d]} : GasTab{nullptr, 0};
+}
+
+// the segment holding r: the last k <= n - 2 with r_k <= r, 0 below r_1 (the
+// end segments extend beyond the table)
+__device__ __forceinline__ int gas_segment(const GasTab &t, double r)
+{
+    int lo = 0, hi = t.n - 1;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (t.k[mid].r <= r)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
 
 __device__ inline double mpow(double x, double y) { return pow(x, y); }
 __device__ inline float mpow(float x, float y) { return powf(x, y); }
@@ -103,15 +136,34 @@ __device__ inline float mlog(float x) { return logf(x); }
 __device__ inline double mexpm1(double x) { return expm1(x); }
 __device__ inline float mexpm1(float x) { return expm1f(x); }
 
-// all quantities of the static power-law, vertically isothermal disk
+// all quantities of the static, vertically isothermal disk: power laws in r,
+// or log-log interpolation of the disk's gas table
 template <class T>
-__device__ inline Gas<T> gas_at(const mcd_disk_params &P, double r, double z)
+__device__ inline Gas<T> gas_at(const mcd_disk_params &P, GasTab tab, double r, double z)
 {
     Gas<T> g;
-    T x = (T)r * (T)(1.0 / kAU);
     T rr = (T)r, zz = (T)z;
-    g.Sigma = (T)P.sigma0 * mpow(x, -(T)P.p);
-    g.T_ = (T)P.T0 * mpow(x, -(T)P.q);
+    if (tab.n >= 2) {
+        const GasKnot &K = tab.k[gas_segment(tab, r)];
+        if constexpr (sizeof(T) == 8) {
+            const double dl = log(r) - K.lnr;
+            g.Sigma = exp(K.lnS - K.p * dl);
+            g.T_ = exp(K.lnT - K.q * dl);
+        } else {
+            // ln(r / r_k) from the ratio: exact to a few float ulps of a small number
+            const float dl = logf((float)r / (float)K.r);
+            g.Sigma = (float)K.S * expf(-(float)K.p * dl);
+            g.T_ = (float)K.T * expf(-(float)K.q * dl);
+        }
+        g.p = (T)K.p;
+        g.q = (T)K.q;
+    } else {
+        T x = (T)r * (T)(1.0 / kAU);
+        g.Sigma = (T)P.sigma0 * mpow(x, -(T)P.p);
+        g.T_ = (T)P.T0 * mpow(x, -(T)P.q);
+        g.p = (T)P.p;
+        g.q = (T)P.q;
+    }
     g.cs = msqrt((T)kKB * g.T_ / ((T)P.mu * (T)kMP));
     g.Omega = msqrt((T)(P.m_star * kGMsun) / rr / rr / rr);
     g.H = g.cs / g.Omega;
@@ -121,12 +173,18 @@ __device__ inline Gas<T> gas_at(const mcd_disk_params &P, double r, double z)
     g.vth = (T)1.5957691216057308 * g.cs;  // sqrt(8/pi)
     g.lambda = ((T)P.mu * (T)kMP / (T)P.sigma_h2) / g.rho;
     g.nu = (T)0.5 * g.vth * g.lambda;
-    g.etavk = (T)0.5 * g.cs * g.cs / (g.Omega * rr) * ((T)P.p + (T)0.5 * ((T)3 + (T)P.q));
+    g.etavk = (T)0.5 * g.cs * g.cs / (g.Omega * rr) * (g.p + (T)0.5 * ((T)3 + g.q));
     g.D = (T)P.alpha * g.cs * g.H;
     g.vg2 = (T)1.5 * (T)P.alpha * g.cs * g.cs;
     g.St_eta = (T)1 / msqrt(g.D / g.nu);
     g.asw = (T)2.25 * g.lambda;
     return g;
+}
+
+template <class T>
+__device__ inline Gas<T> gas_at(const mcd_disk_params &P, double r, double z)
+{
+    return gas_at<T>(P, GasTab{nullptr, 0}, r, z);
 }
 
 __host__ __device__ inline double monomer_mass(const mcd_disk_params &P)
@@ -211,6 +269,8 @@ struct mcd_ctx {
     double *diag_edges = nullptr, *diag_out = nullptr;  // diagnostics: bin edges, per-bin sums
     unsigned long long *map_acc = nullptr;  // sigma map: per-bin unit counts, then the unit's exponent
     double *map_redges = nullptr, *map_medges = nullptr, *map_out = nullptr;
+    mcd::GasKnot *gas_knots = nullptr;  // [n_disks][MCD_MAX_GAS_KNOTS] gas tables
+    int32_t *gas_n = nullptr;           // knots per disk (0: the power laws)
     static constexpr int64_t kLogCap = 1 << 16;
 
     // options
@@ -221,6 +281,8 @@ struct mcd_ctx {
     int32_t smem_optin = 0;  // dynamic shared memory the stored-dv collide variant may request
     int32_t ramp = 0;        // some disk has a fragmentation ramp (frag_ramp > 0)
     int32_t tracer = 0;      // the swarms carry the tracer column (MCD_OPT_TRACER / mcd_set_tracer)
+    int32_t gas_tables = 0;  // disks with a gas table (mcd_set_gas_table)
+    std::vector<int32_t> gas_n_host;  // knots per disk, as on the device
     int64_t log_cell = -1;
 
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};

@@ -399,6 +399,8 @@ struct ZoneArgs {
     int64_t zcap;   // elements per buffer (the largest zone)
     int radix;      // 1: radix sort in two buffers (zcap <= kZoneRadixMax); 0: bitonic in one
     int id_passes;  // radix path: bytes of the largest id
+    const GasKnot *gas_knots;  // gas tables (a single particle's cell spans H_g)
+    const int32_t *gas_n;
 };
 
 __global__ void __launch_bounds__(kZoneThreads, 2) k_zone(ZoneArgs A)
@@ -493,7 +495,7 @@ __global__ void __launch_bounds__(kZoneThreads, 2) k_zone(ZoneArgs A)
             double rf = key_value(rk[zs]), rl = key_value(rk[zs + nk - 1]);
             int64_t nonempty = Na < nr ? Na : nr;
             if (Na == 1) {
-                double H = gas_at<double>(A.params[d], rf, 0.0).H;
+                double H = gas_at<double>(A.params[d], gas_tab(A.gas_knots, A.gas_n, d), rf, 0.0).H;
                 rlo = __dsub_rn(rf, __dmul_rn(0.5, H));
                 rhi = __dadd_rn(rf, __dmul_rn(0.5, H));
             } else {
@@ -520,7 +522,7 @@ __global__ void __launch_bounds__(kZoneThreads, 2) k_zone(ZoneArgs A)
         if (nc > 0) {
             double zf = key_value(el_key(el[cs])), zl = key_value(el_key(el[cs + nc - 1]));
             if (nk == 1) {
-                double H = gas_at<double>(A.params[d], rcen, 0.0).H;
+                double H = gas_at<double>(A.params[d], gas_tab(A.gas_knots, A.gas_n, d), rcen, 0.0).H;
                 zlo = __dsub_rn(zf, __dmul_rn(0.5, H));
                 zhi = __dadd_rn(zf, __dmul_rn(0.5, H));
             } else {
@@ -654,6 +656,8 @@ cudaError_t launch_regrid(mcd_ctx *c)
     A.zcap = zp.zcap;
     A.radix = zp.radix;
     A.id_passes = zp.id_passes;
+    A.gas_knots = c->gas_knots;
+    A.gas_n = c->gas_n;
     k_zone<<<(unsigned)c->Z, kZoneThreads, zp.smem, st>>>(A);
     k_dead_tail<<<gN, 256, 0, st>>>(c->d_disks, c->slot_disk, c->N, c->n_alive, c->val[0], c->m[b], c->M[b], c->r[b],
                                     c->z[b], c->id[b], c->m[nb], c->M[nb], c->r[nb], c->z[nb], c->id[nb],

@@ -57,18 +57,18 @@ __global__ void k_init(const mcd_disk_params *params, const DiskDev *disks, int 
 }
 
 // ---- transport -------------------------------------------------------------------------
-__device__ __forceinline__ void transport_fp64(const mcd_disk_params &P, double &r, double &z, double m,
-                                               double dt, U4 x, bool &removed)
+__device__ __forceinline__ void transport_fp64(const mcd_disk_params &P, GasTab tab, double &r, double &z,
+                                               double m, double dt, U4 x, bool &removed)
 {
     double rho_bm = sqrt(-2.0 * log(u01d(x.x[0])));
     double ang = 2.0 * kPI * u01d(x.x[1]);
     double xi1 = rho_bm * cos(ang), xi2 = rho_bm * sin(ang);
     double r0 = r, z0 = z;
-    Gas<double> g = gas_at<double>(P, r0, z0);
+    Gas<double> g = gas_at<double>(P, tab, r0, z0);
     double rho_s = P.rho_s;
     double rho_st = g.rho, vth = g.vth, nu = g.nu, asw = g.asw;
     if (P.tr_flags & MCD_TR_ST_MIDPLANE) {
-        Gas<double> g0 = gas_at<double>(P, r0, 0.0);
+        Gas<double> g0 = gas_at<double>(P, tab, r0, 0.0);
         rho_st = g0.rho, vth = g0.vth, nu = g0.nu, asw = g0.asw;
     }
     double a = cbrt(3.0 * m / (4.0 * kPI * rho_s));
@@ -77,7 +77,7 @@ __device__ __forceinline__ void transport_fp64(const mcd_disk_params &P, double 
     if (P.tr_flags & MCD_TR_RADIAL) {
         double vr = -2.0 * g.etavk * St / (1.0 + St * St);
         double s2 = z0 / g.H;
-        double vD = g.D / r0 * (1.0 - P.p - 0.5 * P.q + s2 * s2 * 0.5 * (3.0 - P.q));
+        double vD = g.D / r0 * (1.0 - g.p - 0.5 * g.q + s2 * s2 * 0.5 * (3.0 - g.q));
         rn = r0 + (vr + vD) * dt + sqrt(2.0 * g.D * dt) * xi1;
     }
     if (P.tr_flags & MCD_TR_VERTICAL) {
@@ -96,19 +96,19 @@ __device__ __forceinline__ void transport_fp64(const mcd_disk_params &P, double 
     z = zn;
 }
 
-__device__ __forceinline__ void transport_mixed(const mcd_disk_params &P, double &r, double &z, double m,
-                                                double dt, U4 x, bool &removed)
+__device__ __forceinline__ void transport_mixed(const mcd_disk_params &P, GasTab tab, double &r, double &z,
+                                                double m, double dt, U4 x, bool &removed)
 {
     float rho_bm = sqrtf(-2.0f * logf(u01f(x.x[0])));
     float sn, cs;
     sincospif(2.0f * u01f(x.x[1]), &sn, &cs);
     float xi1 = rho_bm * cs, xi2 = rho_bm * sn;
     double r0 = r, z0 = z;
-    Gas<float> g = gas_at<float>(P, r0, z0);
+    Gas<float> g = gas_at<float>(P, tab, r0, z0);
     float rho_s = (float)P.rho_s;
     float rho_st = g.rho, vth = g.vth, nu = g.nu, asw = g.asw;
     if (P.tr_flags & MCD_TR_ST_MIDPLANE) {
-        Gas<float> g0 = gas_at<float>(P, r0, 0.0);
+        Gas<float> g0 = gas_at<float>(P, tab, r0, 0.0);
         rho_st = g0.rho, vth = g0.vth, nu = g0.nu, asw = g0.asw;
     }
     float a = cbrtf((float)(m * (3.0 / (4.0 * kPI * P.rho_s))));
@@ -118,7 +118,7 @@ __device__ __forceinline__ void transport_mixed(const mcd_disk_params &P, double
     if (P.tr_flags & MCD_TR_RADIAL) {
         float vr = -2.0f * g.etavk * St / (1.0f + St * St);
         float s2 = (float)z0 / g.H;
-        float vD = g.D / (float)r0 * (1.0f - (float)P.p - 0.5f * (float)P.q + s2 * s2 * 0.5f * (3.0f - (float)P.q));
+        float vD = g.D / (float)r0 * (1.0f - g.p - 0.5f * g.q + s2 * s2 * 0.5f * (3.0f - g.q));
         rn = r0 + (double)((vr + vD) * dtf + sqrtf(2.0f * g.D * dtf) * xi1);
     }
     if (P.tr_flags & MCD_TR_VERTICAL) {
@@ -138,8 +138,10 @@ __device__ __forceinline__ void transport_mixed(const mcd_disk_params &P, double
     z = zn;
 }
 
-template <bool MIXED>
-__global__ void __launch_bounds__(256) k_transport(const mcd_disk_params *params, const DiskDev *disks, int nd,
+// TABLE: some disk has a gas table (the variant without one reads none)
+template <bool MIXED, bool TABLE>
+__global__ void __launch_bounds__(256) k_transport(const mcd_disk_params *params, const GasKnot *gas_knots,
+                                                   const int32_t *gas_n, const DiskDev *disks, int nd,
                                                    uint64_t seed, const StepState *state, int64_t N, double *r,
                                                    double *z, const double *m, const double *M, const uint32_t *id,
                                                    double *accreted)
@@ -154,10 +156,11 @@ __global__ void __launch_bounds__(256) k_transport(const mcd_disk_params *params
     double zs = z[s];
     U4 x = philox((uint64_t)id[s], 0, (uint64_t)state->step, kTagTransport, seed, (uint64_t)d);
     bool removed;
+    const GasTab tab = TABLE ? gas_tab(gas_knots, gas_n, d) : GasTab{nullptr, 0};
     if (MIXED)
-        transport_mixed(P, rs, zs, m[s], state->dt, x, removed);
+        transport_mixed(P, tab, rs, zs, m[s], state->dt, x, removed);
     else
-        transport_fp64(P, rs, zs, m[s], state->dt, x, removed);
+        transport_fp64(P, tab, rs, zs, m[s], state->dt, x, removed);
     r[s] = rs;
     z[s] = zs;
     if (removed) atomicAdd(&accreted[d], M[s]);
@@ -190,14 +193,16 @@ cudaError_t launch_transport(mcd_ctx *c)
     if (c->N == 0) return cudaSuccess;
     unsigned blocks = (unsigned)((c->N + 255) / 256);
     int b = c->cur;
-    if (c->prec == MCD_MIXED)
-        k_transport<true><<<blocks, 256, 0, c->stream>>>(c->d_params, c->d_disks, c->n_disks, c->seed, c->state,
-                                                         c->N, c->r[b], c->z[b], c->m[b], c->M[b], c->id[b],
-                                                         c->accreted);
+    auto go = [&](auto kernel) {
+        kernel<<<blocks, 256, 0, c->stream>>>(c->d_params, c->gas_knots, c->gas_n, c->d_disks, c->n_disks, c->seed,
+                                              c->state, c->N, c->r[b], c->z[b], c->m[b], c->M[b], c->id[b],
+                                              c->accreted);
+    };
+    const bool mixed = c->prec == MCD_MIXED, table = c->gas_tables > 0;
+    if (mixed)
+        table ? go(k_transport<true, true>) : go(k_transport<true, false>);
     else
-        k_transport<false><<<blocks, 256, 0, c->stream>>>(c->d_params, c->d_disks, c->n_disks, c->seed, c->state,
-                                                          c->N, c->r[b], c->z[b], c->m[b], c->M[b], c->id[b],
-                                                          c->accreted);
+        table ? go(k_transport<false, true>) : go(k_transport<false, false>);
     c->launches += 1;
     return cudaGetLastError();
 }

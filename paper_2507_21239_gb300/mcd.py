@@ -84,6 +84,7 @@ def lib():
         L.mcd_set_tracer.argtypes = [_vp, C.c_int32, _vp, C.c_int32]
         L.mcd_moments.argtypes = [_vp, C.c_int32, C.c_int32, _vp, _vp]
         L.mcd_sigma_map.argtypes = [_vp, C.c_int32, C.c_int32, _vp, C.c_int32, _vp, _vp]
+        L.mcd_set_gas_table.argtypes = [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp]
         L.mcd_set_option.argtypes = [_vp, C.c_int32, C.c_double]
         L.mcd_trace.argtypes = [_vp, C.c_int32]
         L.mcd_trace_read.argtypes = [_vp, _P(C.c_float)]
@@ -234,6 +235,21 @@ def mcd_sigma_map(ctx: int, disk: int, r_edges, m_edges) -> np.ndarray:
     return out
 
 
+MCD_MAX_GAS_KNOTS = 1024
+
+
+def mcd_set_gas_table(ctx: int, disk: int, table):
+    """The disk's gas tabulated in radius: table rows (r, Sigma_g, T), or None
+    for the power laws (see include/mcd.h)."""
+    if table is None:
+        _check(lib().mcd_set_gas_table(ctx, disk, 0, None, None, None), "mcd_set_gas_table")
+        return
+    t = np.asarray(table, dtype=np.float64).reshape(-1, 3)
+    r, S, T = (np.ascontiguousarray(t[:, k]) for k in range(3))
+    _check(lib().mcd_set_gas_table(ctx, disk, t.shape[0], r.ctypes.data, S.ctypes.data, T.ctypes.data),
+           "mcd_set_gas_table")
+
+
 def mcd_get_tracer(ctx: int, disk: int, q, where: int = MCD_HOST):
     _check(lib().mcd_get_tracer(ctx, disk, _ptr(q), where), "mcd_get_tracer")
 
@@ -310,6 +326,9 @@ class Disk:
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
         self.stream = stream
         self.ctx = mcd_init_disk(params, grids, seed, self.prec, self.workspace, stream)
+        for d, p in enumerate([params] if isinstance(params, dict) else params):
+            if p.get("gas_table") is not None:  # after the initial draw, which keeps the power laws
+                self.set_gas_table(p["gas_table"], d)
 
     def step(self, dt: float):
         mcd_step(self.ctx, dt)
@@ -333,6 +352,9 @@ class Disk:
 
     def set_tracer(self, q, disk: int = 0):
         mcd_set_tracer(self.ctx, disk, np.ascontiguousarray(q, dtype=np.float64))
+
+    def set_gas_table(self, table, disk: int = 0):
+        mcd_set_gas_table(self.ctx, disk, table)
 
     def moments(self, edges, disk: int = 0) -> np.ndarray:
         return mcd_moments(self.ctx, disk, edges)

@@ -116,3 +116,25 @@ def midrun_state(params: dict, N: int, seed: int, a_max_1au: float = 10.0, a_slo
     h = 0.0334 * AU * (r / AU) ** 1.25 / np.sqrt(1.0 + a / settle_a)
     z = rng.normal(size=N) * h
     return m, r, z
+
+
+# ---- a gas disk tabulated in radius -------------------------------------
+def gap_bump_gas_table(params: dict, n: int = 64, r_lo_au: float = 1.5, r_hi_au: float = 80.0,
+                       noise: float = 0.0, seed: int = 0) -> np.ndarray:
+    """Knots (r, Sigma_g, T), an (n, 3) array: a synthetic stand-in for the
+    azimuthally averaged profile of a hydrodynamic snapshot (no snapshot data
+    is at hand).  The disk's power laws with a gap at 10 AU (surface density
+    down by 90 %, as a planet carves one), a pressure bump at 20 AU (three
+    times the background), a temperature break at 10 AU (slope q inside,
+    q + 1/4 outside) and, if noise > 0, seeded relative noise of that size on
+    every knot.  Knots are log-spaced over [r_lo_au, r_hi_au]."""
+    x = np.geomspace(r_lo_au, r_hi_au, n)
+    S = params["sigma0"] * x ** -params["p"]
+    S = S * (1 - 0.9 * np.exp(-((x - 10.0) ** 2) / (2 * 1.5**2))) * (1 + 3.0 * np.exp(-((x - 20.0) ** 2) / (2 * 2.0**2)))
+    q = params["q"]
+    T = np.where(x < 10.0, params["T0"] * x**-q, params["T0"] * 10.0**-q * (x / 10.0) ** -(q + 0.25))
+    if noise > 0:
+        rng = np.random.default_rng(seed)
+        S = S * (1 + noise * rng.standard_normal(n))
+        T = T * (1 + noise * rng.standard_normal(n))
+    return np.c_[x * AU, S, T]
