@@ -167,8 +167,8 @@ int mcd_regrid(mcd_ctx *ctx);
 int mcd_step(mcd_ctx *ctx, double dt);
 
 /*
- * A tracked property per swarm (SURVEY's extra tracked properties, e.g. a
- * composition fraction), carried by the representative particle through the
+ * A tracked property per swarm (a particle history such as a composition
+ * fraction, Statement of Need section), carried by the representative particle through the
  * regrid and updated at every collision (a reading: the paper names no rule):
  * sticking mixes by mass, (m_i q_i + g q_j) / (m_i + g) with g the absorbed
  * mass; fragmentation gives the pair's mass-weighted mixture; erosion leaves the

@@ -126,12 +126,21 @@ def lib():
                                 C.c_double, C.c_int64, C.c_int64, C.c_uint64, C.c_uint64, C.c_int64, C.c_int64,
                                 _d, _i64, C.c_int32]
         L.orc_sigma_map.argtypes = [C.c_int64, _d, _d, _d, C.c_int32, _d, C.c_int32, _d, _d]
+        L.orc_adaptive_dt.argtypes = [_P(Params), C.c_int64, _i64, _d, C.c_int64, _d, _d, _d, C.c_double,
+                                      C.c_double]
+        L.orc_adaptive_dt.restype = C.c_double
+        L.orc_run_adaptive.argtypes = [_P(Params), C.c_int32, C.c_int32, C.c_int64, _d, _d, _d, _d, _u32, _d,
+                                       C.c_double, C.c_double, C.c_double, C.c_int64, C.c_int64, C.c_uint64,
+                                       C.c_uint64, C.c_int64, C.c_int64, _d, _i64, C.c_int32, _d]
         _lib = L
     return _lib
 
 
 def _ptr(a, ct):
     return a.ctypes.data_as(_P(ct)) if a is not None else None
+
+
+YR = 3.15576e7  # Julian year [s] (the oracle's ORC_YR)
 
 
 def _f64(a):
@@ -283,12 +292,22 @@ def collide_all(params: dict, n_r, n_z, off, cb, cv, s: DiskState, t0, t_end, se
 
 
 def run(params: dict, n_r: int, n_z: int, s: DiskState, t0: float, dt: float, step0: int, n_steps: int,
-        seed: int, disk: int = 0, max_events=NO_CAP, rebuild_every=0, nthreads=0):
-    """n_steps of regrid -> collide -> transport, in place; returns status."""
+        seed: int, disk: int = 0, max_events=NO_CAP, rebuild_every=0, nthreads=0, dt_max=None, courant=0.5,
+        dts=None):
+    """n_steps of regrid -> collide -> transport, in place; returns status.
+    dt <= 0: the adaptive step, at most dt_max (default one year), each
+    step's dt written to dts (an n_steps array) when given."""
     acc = np.zeros(1)
     ev = np.zeros(1, np.int64)
     P = Params.from_dict(params)
-    if s.q is None:
+    if not dt > 0:
+        out = np.zeros(n_steps) if dts is None else dts
+        st = lib().orc_run_adaptive(C.byref(P), n_r, n_z, s.m.size, _ptr(s.m, C.c_double), _ptr(s.M, C.c_double),
+                                    _ptr(s.r, C.c_double), _ptr(s.z, C.c_double), _ptr(s.id, C.c_uint32),
+                                    _ptr(s.q, C.c_double), t0, YR if dt_max is None else dt_max, courant, step0,
+                                    n_steps, seed, disk, max_events, rebuild_every, _ptr(acc, C.c_double),
+                                    _ptr(ev, C.c_int64), nthreads, _ptr(out, C.c_double))
+    elif s.q is None:
         st = lib().orc_run(C.byref(P), n_r, n_z, s.m.size, _ptr(s.m, C.c_double), _ptr(s.M, C.c_double),
                            _ptr(s.r, C.c_double), _ptr(s.z, C.c_double), _ptr(s.id, C.c_uint32), t0, dt, step0,
                            n_steps, seed, disk, max_events, rebuild_every, _ptr(acc, C.c_double),
@@ -301,6 +320,16 @@ def run(params: dict, n_r: int, n_z: int, s: DiskState, t0: float, dt: float, st
     s.accreted += float(acc[0])
     s.events += int(ev[0])
     return st
+
+
+def adaptive_dt(params: dict, cell_off, cell_b, s: DiskState, dt_max: float, courant: float = 0.5) -> float:
+    """The adaptive step for the cells (cell_off, cell_b) of a regrid of s."""
+    off = np.ascontiguousarray(cell_off, dtype=np.int64)
+    cb = _f64(np.ascontiguousarray(cell_b).reshape(-1))
+    P = Params.from_dict(params)
+    return lib().orc_adaptive_dt(C.byref(P), off.size - 1, _ptr(off, C.c_int64), _ptr(cb, C.c_double), s.m.size,
+                                 _ptr(s.m, C.c_double), _ptr(s.r, C.c_double), _ptr(s.z, C.c_double), dt_max,
+                                 courant)
 
 
 def moments(m, M, r, edges):

@@ -461,8 +461,8 @@ static double orc_outcome(const orc_params *P, double mi, double mj, double dv, 
 }
 
 /* A tracked property of each swarm (a composition fraction q), carried by its
- * representative particle (SURVEY's extra tracked properties; reading, the
- * paper gives no rule): sticking mixes by mass, q_i <- (m_i q_i + g q_j) /
+ * representative particle (the particle histories of the Statement of Need
+ * section; reading, the paper gives no rule): sticking mixes by mass, q_i <- (m_i q_i + g q_j) /
  * (m_i + g), g = N_g m_j the absorbed mass; fragmentation gives the pair's
  * mass-weighted mixture; erosion leaves the larger body's q as it was and turns
  * the smaller one into debris of itself and the chipped mass, chi times its own:
@@ -817,6 +817,37 @@ void orc_transport(const orc_params *P, int64_t N, double *r, double *z, const d
     if (accreted) *accreted += acc;
 }
 
+/* ---- adaptive time step (reading; the paper states no rule) -------------
+ * dt = min(dt_max, C min_c (r_hi - r_lo)_c / max_i |v_r,i|): a drifting
+ * particle crosses at most the fraction C of the narrowest cell in one step.
+ * The minimum runs over the cells that hold particles, the maximum over the
+ * live particles, with v_r = -2 eta v_K St / (1 + St^2) the radial drift of the
+ * transport step (St at the particle, or at the midplane with
+ * ORC_TR_ST_MIDPLANE).  Without radial transport (or in the constant-kernel
+ * mode) nothing drifts and dt = dt_max. */
+double orc_adaptive_dt(const orc_params *P, int64_t ncell, const int64_t *cell_off, const double *cell_b,
+                       int64_t N, const double *m, const double *r, const double *z, double dt_max, double courant)
+{
+    if (P->kernel_mode != 0 || !(P->tr_flags & ORC_TR_RADIAL)) return dt_max;
+    double dr_min = INFINITY, v_max = 0.0;
+    for (int64_t c = 0; c < ncell; ++c)
+        if (cell_off[c + 1] > cell_off[c]) {
+            double w = cell_b[6 * c + 1] - cell_b[6 * c];
+            if (w < dr_min) dr_min = w;
+        }
+    for (int64_t k = 0; k < N; ++k) {
+        if (!isfinite(r[k])) continue;
+        orc_gas g = orc_gas_at(P, r[k], z[k]);
+        orc_gas gs = (P->tr_flags & ORC_TR_ST_MIDPLANE) ? orc_gas_at(P, r[k], 0.0) : g;
+        double St = orc_particle(P, &gs, m[k]).St;
+        double v = fabs(-2.0 * g.etavk * St / (1.0 + St * St));
+        if (v > v_max) v_max = v;
+    }
+    if (!(v_max > 0.0)) return dt_max;
+    double dt = courant * dr_min / v_max;
+    return dt < dt_max ? dt : dt_max;
+}
+
 /* ======================================================================== */
 /* Whole-disk driver: regrid -> collide every cell to t + dt -> transport.  */
 /* ======================================================================== */
@@ -861,7 +892,7 @@ int orc_collide_all(const orc_params *P, int32_t n_r, int32_t n_z, const int64_t
 static int orc_run_impl(const orc_params *P, int32_t n_r, int32_t n_z, int64_t N, double *m, double *M, double *r,
                         double *z, uint32_t *id, double *q, double t0, double dt, int64_t step0, int64_t n_steps,
                         uint64_t seed, uint64_t disk, int64_t max_events, int64_t rebuild_every, double *accreted,
-                        int64_t *events_total, int32_t nthreads)
+                        int64_t *events_total, int32_t nthreads, double dt_max, double courant, double *dts)
 {
     int64_t ncell = (int64_t)n_r * n_z;
     int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (ncell + 1));
@@ -881,13 +912,16 @@ static int orc_run_impl(const orc_params *P, int32_t n_r, int32_t n_z, int64_t N
             for (int64_t k = 0; k < N; ++k) qt[k] = q[perm[k]];
             memcpy(q, qt, sizeof(double) * N);
         }
-        status = orc_collide_all_impl(P, n_r, n_z, off, cb, cv, m, M, q, t, t + dt, seed, disk, step, max_events,
+        /* dt <= 0: the adaptive step, from the cells just made */
+        const double h = dt > 0.0 ? dt : orc_adaptive_dt(P, ncell, off, cb, N, m, r, z, dt_max, courant);
+        if (dts) dts[s] = h;
+        status = orc_collide_all_impl(P, n_r, n_z, off, cb, cv, m, M, q, t, t + h, seed, disk, step, max_events,
                                       rebuild_every, ce, nthreads);
         for (int64_t c = 0; c < ncell; ++c)
             if (events_total) *events_total += ce[c];
         if (P->kernel_mode == 0 && (P->tr_flags & (ORC_TR_RADIAL | ORC_TR_VERTICAL)))
-            orc_transport(P, N, r, z, m, M, id, dt, seed, disk, step, accreted);
-        t += dt;
+            orc_transport(P, N, r, z, m, M, id, h, seed, disk, step, accreted);
+        t += h;
     }
     free(off); free(cb); free(cv); free(ce); free(perm); free(qt);
     return status;
@@ -898,7 +932,7 @@ int orc_run(const orc_params *P, int32_t n_r, int32_t n_z, int64_t N, double *m,
             int64_t max_events, int64_t rebuild_every, double *accreted, int64_t *events_total, int32_t nthreads)
 {
     return orc_run_impl(P, n_r, n_z, N, m, M, r, z, id, NULL, t0, dt, step0, n_steps, seed, disk, max_events,
-                        rebuild_every, accreted, events_total, nthreads);
+                        rebuild_every, accreted, events_total, nthreads, 0.0, 0.0, NULL);
 }
 
 int orc_run_q(const orc_params *P, int32_t n_r, int32_t n_z, int64_t N, double *m, double *M, double *r, double *z,
@@ -907,7 +941,17 @@ int orc_run_q(const orc_params *P, int32_t n_r, int32_t n_z, int64_t N, double *
               int32_t nthreads)
 {
     return orc_run_impl(P, n_r, n_z, N, m, M, r, z, id, q, t0, dt, step0, n_steps, seed, disk, max_events,
-                        rebuild_every, accreted, events_total, nthreads);
+                        rebuild_every, accreted, events_total, nthreads, 0.0, 0.0, NULL);
+}
+
+/* n_steps with the adaptive step (dt_max, courant); dts[n_steps] receives each step's dt; q may be NULL */
+int orc_run_adaptive(const orc_params *P, int32_t n_r, int32_t n_z, int64_t N, double *m, double *M, double *r,
+                     double *z, uint32_t *id, double *q, double t0, double dt_max, double courant, int64_t step0,
+                     int64_t n_steps, uint64_t seed, uint64_t disk, int64_t max_events, int64_t rebuild_every,
+                     double *accreted, int64_t *events_total, int32_t nthreads, double *dts)
+{
+    return orc_run_impl(P, n_r, n_z, N, m, M, r, z, id, q, t0, 0.0, step0, n_steps, seed, disk, max_events,
+                        rebuild_every, accreted, events_total, nthreads, dt_max, courant, dts);
 }
 
 /* ---- diagnostics --------------------------------------------------------

@@ -815,3 +815,61 @@ def test_gas_table_radial_step_mean(zH):
     se = np.sqrt(2 * gz["D"][0] * dt / n)
     assert abs(dr.mean() - (vr + vD) * dt) < 5 * se
     assert abs(vD * dt) > 15 * se
+
+
+# ---- the adaptive time step --------------------------------------------------
+@pytest.mark.parametrize("N,grid", [(600, (10, 3)), (20, (10, 3))])
+def test_adaptive_dt_brute_force(N, grid):
+    """dt = min(dt_max, C min_c dr_c / max_i |v_r,i|) against a numpy statement
+    built from pinned parts: the regrid's cells (empty ones excluded), St from
+    the particle function (at the particle, or at the midplane), eta v_K from
+    the gas function; a removed particle does not count; without radial
+    transport, or in the constant-kernel mode, dt = dt_max."""
+    P = W.benchmark_disk()
+    m, r, z = W.midrun_state(P, N, seed=3)
+    r[5] = np.inf
+    s = oracle.DiskState(m, np.full(N, 1e26), r, z, np.arange(N, dtype=np.uint32))
+    st, _, off, cb, _, _ = oracle.regrid(P, grid[0], grid[1], s)
+    assert st == 0
+    nonempty = np.diff(off) > 0
+    assert N > 100 or not nonempty.all()  # the small case has empty cells
+    dr = (cb[:, 1] - cb[:, 0])[nonempty].min()
+    for flags in (W.TR_RADIAL | W.TR_VERTICAL, W.TR_RADIAL | W.TR_ST_MIDPLANE):
+        Pf = dict(P, tr_flags=flags)
+        v = []
+        for k in np.flatnonzero(np.isfinite(s.r)):
+            zs = 0.0 if flags & W.TR_ST_MIDPLANE else s.z[k]
+            St = oracle.particle(Pf, s.r[k], zs, s.m[k])[1][0]
+            eta = oracle.gas(Pf, s.r[k], s.z[k])["etavk"][0]
+            v.append(abs(2 * eta * St / (1 + St**2)))
+        ref = 0.5 * dr / max(v)
+        for dt_max in (1e30, 0.5 * ref):
+            got = oracle.adaptive_dt(Pf, off, cb, s, dt_max, 0.5)
+            assert got == pytest.approx(min(dt_max, ref), rel=1e-13)
+        assert oracle.adaptive_dt(Pf, off, cb, s, 1e30, 0.25) == pytest.approx(0.5 * ref, rel=1e-13)
+    assert oracle.adaptive_dt(dict(P, tr_flags=W.TR_VERTICAL), off, cb, s, 7.0) == 7.0
+    assert oracle.adaptive_dt(W.constant_kernel_cell(), off, cb, s, 7.0) == 7.0
+
+
+def test_adaptive_run_equals_fixed_steps_of_its_dts():
+    """A run with the adaptive step equals, bit for bit, fixed-step runs of the
+    step sizes it chose, and each chosen step is the adaptive step of the state
+    it started from."""
+    P = W.benchmark_disk()
+    N, grid, seed, dt_max = 20 * 2 * 10, (20, 2), 4, 1e4 * YR
+    m, r, z = W.midrun_state(P, N, seed=8)  # grains that drift
+    a = oracle.DiskState(m, np.full(N, 1e26), r, z, np.arange(N, dtype=np.uint32))
+    b = oracle.DiskState(m.copy(), a.M.copy(), r.copy(), z.copy(), a.id.copy())
+    dts = np.zeros(4)
+    assert oracle.run(P, *grid, a, 0.0, 0.0, 0, 4, seed, dt_max=dt_max, dts=dts) == 0
+    assert np.all(dts > 0) and np.all(dts < dt_max)
+    t = 0.0
+    for k in range(4):
+        c = oracle.DiskState(b.m.copy(), b.M.copy(), b.r.copy(), b.z.copy(), b.id.copy())
+        _, _, off, cb, _, _ = oracle.regrid(P, *grid, c)
+        assert oracle.adaptive_dt(P, off, cb, c, dt_max) == dts[k]
+        assert oracle.run(P, *grid, b, t, dts[k], k, 1, seed) == 0
+        t += dts[k]
+    for key in ("m", "r", "z", "id"):
+        assert np.array_equal(getattr(a, key), getattr(b, key)), key
+    assert a.events == b.events and a.accreted == b.accreted
