@@ -120,6 +120,8 @@ typedef struct mcd_ctx mcd_ctx;
                                    Both give bit-identical results (default 1) */
 #define MCD_OPT_TRACER 11       /* 1: every swarm carries the tracer column (mcd_get_tracer); 0 (default)
                                    clears it.  mcd_set_tracer switches it on. */
+#define MCD_OPT_DT_MAX 12       /* the largest step mcd_step(dt <= 0) takes [s] (default one year) */
+#define MCD_OPT_COURANT 13      /* C of the adaptive step (default 0.5) */
 
 /*
  * Bytes of device workspace needed for n_disks disks at precision prec.
@@ -163,7 +165,19 @@ int mcd_transport(mcd_ctx *ctx, double dt);
  */
 int mcd_regrid(mcd_ctx *ctx);
 
-/* One step: regrid, collide to t + dt, transport dt (dt > 0). */
+/*
+ * One step: regrid, collide to t + dt, transport dt (Summary section: binning,
+ * collisional evolution, transport).  dt > 0: that step.  dt <= 0: the step is
+ * chosen on the device after the regrid (a reading; the paper gives no rule):
+ * per disk min(dt_max, C min_c (r_hi - r_lo)_c / max_i |v_r,i|) over the cells
+ * that hold particles and the live particles, v_r = -2 eta v_K St / (1 + St^2)
+ * the radial drift of the transport step; a disk without radial transport asks
+ * for dt_max.  The disks of a context share one clock, so the step is the
+ * smallest of theirs.  dt_max and C are MCD_OPT_DT_MAX and MCD_OPT_COURANT;
+ * the mixed path evaluates v_r in FP32 like its transport.  The host learns
+ * the clock from mcd_get_stats (t); the first mcd_collide after adaptive steps
+ * synchronises once to read it.  NaN or infinite dt: MCD_EINVAL.
+ */
 int mcd_step(mcd_ctx *ctx, double dt);
 
 /*

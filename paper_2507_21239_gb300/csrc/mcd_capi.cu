@@ -127,6 +127,7 @@ size_t carve(mcd_ctx *c, void *base, const Sizes &S, int32_t nd)
     x->map_out = cv.take<double>(MCD_MAX_MAP_BINS);
     x->gas_knots = cv.take<GasKnot>((size_t)nd * kMaxGasKnots);
     x->gas_n = cv.take<int32_t>(nd);
+    x->dt_acc = cv.take<unsigned long long>(2 * (size_t)nd + 1);
     return (cv.off + 255) & ~(size_t)255;
 }
 
@@ -177,6 +178,7 @@ cudaError_t enqueue_step_body(mcd_ctx *c)
     if (e == cudaSuccess) e = mark(c, 1);
     if (e == cudaSuccess && c->lpt) e = launch_lpt(c);
     if (e == cudaSuccess) e = mark(c, 2);
+    if (e == cudaSuccess && c->graph_adaptive) e = launch_adaptive_dt(c);
     if (e == cudaSuccess) e = launch_collide_impl(c, 1, 0.0);
     if (e == cudaSuccess) e = mark(c, 3);
     if (e == cudaSuccess) e = launch_transport(c);
@@ -261,6 +263,8 @@ int mcd_init_disk(mcd_ctx **out, const mcd_disk_params *p, const mcd_grid *g, in
     if (e == cudaSuccess) e = cudaMemsetAsync(c->cell_events, 0, 8 * S.C, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->log_n, 0, 8, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->gas_n, 0, 4 * n_disks, st);  // the power laws
+    const std::vector<unsigned long long> rest = adaptive_dt_rest(n_disks);
+    cp(c->dt_acc, rest.data(), 8 * rest.size());
     for (int b = 0; b < 2; ++b)  // the tracer starts at zero (uniform: its order does not matter)
         if (e == cudaSuccess) e = cudaMemsetAsync(c->q[b], 0, 8 * S.N, st);
     if (e == cudaSuccess) e = prepare_collide(c);
@@ -287,7 +291,16 @@ int mcd_regrid(mcd_ctx *c)
 
 int mcd_collide(mcd_ctx *c, double t_end)
 {
-    if (!c || !(t_end >= c->t_host)) return MCD_EINVAL;
+    if (!c) return MCD_EINVAL;
+    if (!c->t_known) {  // after adaptive steps the clock lives on the device
+        StepState s;
+        if (cudaMemcpyAsync(&s, c->state, sizeof s, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+            return MCD_ECUDA;
+        c->t_host = s.t;
+        c->t_known = true;
+    }
+    if (!(t_end >= c->t_host)) return MCD_EINVAL;
     if (!c->cells_valid) return MCD_ESTATE;
     cudaError_t e = cudaSuccess;
     if (c->lpt) e = launch_lpt(c);
@@ -312,8 +325,13 @@ int mcd_transport(mcd_ctx *c, double dt)
 
 int mcd_step(mcd_ctx *c, double dt)
 {
-    if (!c || !(dt > 0.0) || !isfinite(dt)) return MCD_EINVAL;
-    cudaError_t e = launch_set_clock(c, 0.0, 0, dt, 1);
+    if (!c || !isfinite(dt)) return MCD_EINVAL;
+    const int32_t adaptive = dt > 0.0 ? 0 : 1;  // dt <= 0: chosen on the device after the regrid
+    if (adaptive != c->graph_adaptive) {
+        drop_graphs(c);
+        c->graph_adaptive = adaptive;
+    }
+    cudaError_t e = adaptive ? cudaSuccess : launch_set_clock(c, 0.0, 0, dt, 1);
     if (e != cudaSuccess) return MCD_ECUDA;
     if (c->use_graph) {
         int p = c->cur;
@@ -356,7 +374,10 @@ int mcd_step(mcd_ctx *c, double dt)
         e = enqueue_step_body(c);
         if (e != cudaSuccess) return MCD_ECUDA;
     }
-    c->t_host += dt;
+    if (adaptive)
+        c->t_known = false;
+    else
+        c->t_host += dt;
     c->step_host += 1;
     c->cells_valid = false;
     return MCD_OK;
@@ -688,6 +709,14 @@ int mcd_set_option(mcd_ctx *c, int32_t key, double v)
         c->tracer = v != 0.0;
         break;
     case MCD_OPT_DV_MATRIX: c->dv_matrix = v != 0.0; break;
+    case MCD_OPT_DT_MAX:
+        if (!(v > 0.0) || !isfinite(v)) return MCD_EINVAL;
+        c->dt_max = v;
+        break;
+    case MCD_OPT_COURANT:
+        if (!(v > 0.0) || !isfinite(v)) return MCD_EINVAL;
+        c->courant = v;
+        break;
     case MCD_OPT_THREADS:
         if (v != 0.0 && (v < c->n_max || v > kMaxCell || ((int)v % 32) != 0)) return MCD_EINVAL;
         c->threads = (int32_t)v;

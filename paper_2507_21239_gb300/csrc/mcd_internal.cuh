@@ -282,6 +282,10 @@ struct mcd_ctx {
     int32_t ramp = 0;        // some disk has a fragmentation ramp (frag_ramp > 0)
     int32_t tracer = 0;      // the swarms carry the tracer column (MCD_OPT_TRACER / mcd_set_tracer)
     int32_t gas_tables = 0;  // disks with a gas table (mcd_set_gas_table)
+    unsigned long long *dt_acc = nullptr;  // adaptive step: per-disk max |v_r| and min width bits, block count
+    double dt_max = 3.15576e7, courant = 0.5;  // the adaptive step's cap [s] and C (MCD_OPT_DT_MAX / COURANT)
+    int32_t graph_adaptive = 0;             // the captured step graphs choose dt on the device
+    bool t_known = true;                    // t_host is the device clock (false after an adaptive step)
     std::vector<int32_t> gas_n_host;  // knots per disk, as on the device
     int64_t log_cell = -1;
 
@@ -305,6 +309,8 @@ cudaError_t launch_lpt(mcd_ctx *c);
 cudaError_t launch_collide_impl(mcd_ctx *c, int t_end_from_state, double t_end);
 cudaError_t launch_set_clock(mcd_ctx *c, double t, int set_t, double dt, int set_dt);
 cudaError_t launch_advance_clock(mcd_ctx *c, int add_dt_to_t);
+cudaError_t launch_adaptive_dt(mcd_ctx *c);  // writes dt into the device state
+std::vector<unsigned long long> adaptive_dt_rest(int32_t n_disks);
 cudaError_t prepare_collide(mcd_ctx *c);
 cudaError_t prepare_zone(mcd_ctx *c);
 cudaError_t launch_moments(mcd_ctx *c, int disk, int nbins);

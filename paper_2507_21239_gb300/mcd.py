@@ -18,7 +18,8 @@ MCD_OK, MCD_EINVAL, MCD_ENOMEM, MCD_ECUDA, MCD_ENAN, MCD_ETIMEOUT, MCD_EEMPTY, M
 MCD_FP64, MCD_MIXED = 0, 1
 MCD_HOST, MCD_DEVICE = 0, 1
 (MCD_OPT_MAX_EVENTS, MCD_OPT_CAP_STOPS, MCD_OPT_REBUILD_EVERY, MCD_OPT_USE_GRAPH, MCD_OPT_DUMP_R,
- MCD_OPT_LOG_CELL, MCD_OPT_LPT, MCD_OPT_THREADS, MCD_OPT_EXCLUSIVE, MCD_OPT_DV_MATRIX, MCD_OPT_TRACER) = range(1, 12)
+ MCD_OPT_LOG_CELL, MCD_OPT_LPT, MCD_OPT_THREADS, MCD_OPT_EXCLUSIVE, MCD_OPT_DV_MATRIX, MCD_OPT_TRACER,
+ MCD_OPT_DT_MAX, MCD_OPT_COURANT) = range(1, 14)
 PREC = {"fp64": MCD_FP64, "mixed": MCD_MIXED}
 
 
