@@ -70,6 +70,21 @@ def batched_disks(n_disks: int = 64, key=(2507, 0xB47C)):
     return disks
 
 
+def ppc_sweep(ppcs=(25, 50, 100, 200, 400), seeds: int = 4, n_r: int = 16, n_z: int = 4, **over):
+    """A resolution sweep for one batched launch: the Benchmark-table disk at
+    every particles-per-cell value in ppcs, `seeds` disks of each (seed k of a
+    resolution is disk k of that resolution's block), n_r x n_z cells.
+    Returns (params list, grid list, ppc of each disk)."""
+    P = benchmark_disk(**over)
+    params, grids, res = [], [], []
+    for ppc in ppcs:
+        for _ in range(seeds):
+            params.append(dict(P))
+            grids.append((n_r, n_z, int(ppc)))
+            res.append(int(ppc))
+    return params, grids, np.array(res)
+
+
 # ---- random inputs for the unit-level parity tests ----------------------
 def random_masses(n: int, seed: int, lo: float = 1e-12, hi: float = 1e4, ties: float = 0.1) -> np.ndarray:
     """Log-uniform masses over [lo, hi] with a fraction of exact repeats and of
