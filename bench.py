@@ -149,11 +149,25 @@ def make_state(args, ctx_or_none, rank):
     return P, grid, N, m, r, z
 
 
-def cpu_oracle_steps(P, grid, state, seed, step0, dt, budget_s, max_steps, min_steps=1):
-    """Time full oracle steps (regrid, collide, transport) on the host cores."""
+def cpu_model() -> str:
+    """The host CPU as the kernel names it (model name, else the architecture)."""
+    import platform
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
+def cpu_oracle_steps(P, grid, state, seed, step0, dt, budget_s, max_steps, min_steps=1, cores=None):
+    """Time full oracle steps (regrid, collide, transport) on the host cores
+    (all of them unless cores is given)."""
     import oracle
-    s = oracle.DiskState(*state)
-    cores = os.cpu_count() or 1
+    s = oracle.DiskState(*[np.copy(a) for a in state])
+    cores = cores or os.cpu_count() or 1
     steps, ev0, t0 = 0, 0, time.perf_counter()
     elapsed = 0.0
     while steps < max_steps and (steps < min_steps or elapsed < budget_s):
@@ -361,9 +375,14 @@ def run_ours(args):
         s = oracle.init_disk(P, N, seed)
         ev, el, steps, cores = cpu_oracle_steps(P, grid, (m, s.M, r, z, s.id), seed, 0, dt,
                                                 budget_s=args.cpu_budget_s, max_steps=50)
+        ev1, el1, steps1, _ = cpu_oracle_steps(P, grid, (m, s.M, r, z, s.id), seed, 0, dt,
+                                               budget_s=0.2 * args.cpu_budget_s, max_steps=10, cores=1)
         out["cpu_baseline"] = {"value": ev / el, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"{steps} full oracle step(s) (dt = {args.dt_yr} yr) of the same "
-                                         f"{N:,}-particle mid-run disk, {el:.1f} s"}
+                                         f"{N:,}-particle mid-run disk, {el:.1f} s",
+                               "cpu": cpu_model(),
+                               "single_core": {"value": ev1 / el1, "unit": UNIT, "cores": 1,
+                                               "sample": f"{steps1} full oracle step(s), {el1:.1f} s"}}
     out["clocks"] = clk.summary()
     if rank == 0:
         print(json.dumps(out), flush=True)
