@@ -115,9 +115,10 @@ typedef struct mcd_ctx mcd_ctx;
 #define MCD_OPT_LPT 7           /* 1: order cells by descending work estimate (default 1) */
 #define MCD_OPT_THREADS 8       /* threads per cell in collide; 0 = auto */
 #define MCD_OPT_EXCLUSIVE 9     /* 1: one collide CTA per SM, so long event chains share no SM (default 1) */
-#define MCD_OPT_DV_MATRIX 10    /* 1: MCD_MIXED keeps each cell's dv_ij matrix in shared memory when it fits
-                                   (cells of up to ~230 particles); 0: recompute row i at every event.
-                                   Both give bit-identical results (default 1) */
+#define MCD_OPT_DV_MATRIX 10    /* 1: keep each cell's dv_ij matrix, MCD_MIXED in shared memory when it fits
+                                   (cells of up to ~230 particles), MCD_FP64 in the workspace when every
+                                   cell's matrix together takes at most 4 GiB; 0: recompute row i at every
+                                   event.  Both give bit-identical results (default 1) */
 #define MCD_OPT_TRACER 11       /* 1: every swarm carries the tracer column (mcd_get_tracer); 0 (default)
                                    clears it.  mcd_set_tracer switches it on. */
 #define MCD_OPT_DT_MAX 12       /* the largest step mcd_step(dt <= 0) takes [s] (default one year) */
@@ -126,6 +127,8 @@ typedef struct mcd_ctx mcd_ctx;
 /*
  * Bytes of device workspace needed for n_disks disks at precision prec.
  * p[n_disks], g[n_disks] host arrays.  Returns MCD_EINVAL on a bad grid.
+ * MCD_FP64 adds, when that is at most 4 GiB, cells x ld^2 doubles for the
+ * stored dv matrices (ld = the largest particles-per-cell rounded up to odd).
  */
 int mcd_workspace_size(const mcd_disk_params *p, const mcd_grid *g, int32_t n_disks, int32_t prec, size_t *bytes);
 

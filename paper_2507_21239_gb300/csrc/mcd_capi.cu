@@ -75,7 +75,17 @@ int plan(const mcd_disk_params *p, const mcd_grid *g, int32_t nd, Sizes &S)
     return MCD_OK;
 }
 
-size_t carve(mcd_ctx *c, void *base, const Sizes &S, int32_t nd)
+// FP64 stored dv matrices (ld x ld doubles per cell, ld = n_max rounded up to
+// odd) are reserved when they take at most this much
+constexpr size_t kFp64MatrixCap = (size_t)4 << 30;
+
+size_t fp64_matrix_bytes(const Sizes &S)
+{
+    const size_t ld = (size_t)(S.n_max | 1);
+    return (size_t)S.C * ld * ld * sizeof(double);
+}
+
+size_t carve(mcd_ctx *c, void *base, const Sizes &S, int32_t nd, int32_t prec)
 {
     Carver cv(base);
     mcd_ctx tmp;
@@ -128,6 +138,8 @@ size_t carve(mcd_ctx *c, void *base, const Sizes &S, int32_t nd)
     x->gas_knots = cv.take<GasKnot>((size_t)nd * kMaxGasKnots);
     x->gas_n = cv.take<int32_t>(nd);
     x->dt_acc = cv.take<unsigned long long>(2 * (size_t)nd + 1);
+    const size_t mb = fp64_matrix_bytes(S);
+    x->dvg = (prec == MCD_FP64 && mb <= kFp64MatrixCap) ? cv.take<double>(mb / sizeof(double)) : nullptr;
     return (cv.off + 255) & ~(size_t)255;
 }
 
@@ -197,7 +209,7 @@ int mcd_workspace_size(const mcd_disk_params *p, const mcd_grid *g, int32_t n_di
     Sizes S;
     int rc = plan(p, g, n_disks, S);
     if (rc) return rc;
-    *bytes = carve(nullptr, nullptr, S, n_disks);
+    *bytes = carve(nullptr, nullptr, S, n_disks, prec);
     return MCD_OK;
 }
 
@@ -210,7 +222,7 @@ int mcd_init_disk(mcd_ctx **out, const mcd_disk_params *p, const mcd_grid *g, in
     Sizes S;
     int rc = plan(p, g, n_disks, S);
     if (rc) return rc;
-    size_t need = carve(nullptr, nullptr, S, n_disks);
+    size_t need = carve(nullptr, nullptr, S, n_disks, prec);
     if (ws_bytes < need) return MCD_ENOMEM;
     mcd_ctx *c = new (std::nothrow) mcd_ctx();
     if (!c) return MCD_ENOMEM;
@@ -229,7 +241,7 @@ int mcd_init_disk(mcd_ctx **out, const mcd_disk_params *p, const mcd_grid *g, in
     c->Z = S.Z;
     c->n_tiles = S.T;
     c->n_max = S.n_max;
-    carve(c, ws, S, n_disks);
+    carve(c, ws, S, n_disks, prec);
     double *d_Mswarm = c->d_Mswarm;
 
     // host-built tables

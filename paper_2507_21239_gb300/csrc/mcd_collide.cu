@@ -606,6 +606,7 @@ struct CollideArgs {
     int64_t n_cells;
     int dv_ld;  // row stride of the stored dv matrix (odd; STORE path)
     double *q;  // the tracer column (TRACER variants)
+    double *dvg;  // FP64 stored matrices in global memory, ld x ld per cell (STORE, FP64)
 };
 
 template <class T>
@@ -656,6 +657,7 @@ __global__ void __launch_bounds__(kMaxCell) k_collide(CollideArgs A)
 
     const int64_t cell = A.queue ? (int64_t)A.queue[blockIdx.x] : (int64_t)blockIdx.x;
     if (cell >= A.n_cells) return;
+    if constexpr (STORE && sizeof(T) == 8) Dm = reinterpret_cast<T *>(A.dvg) + (size_t)cell * ld * ld;
     const int n = A.cell_n[cell];
     const int k = threadIdx.x;
     if (n <= 0) {
@@ -1024,8 +1026,10 @@ static cudaError_t collide_impl(mcd_ctx *cx, int from_state, double t_end)
     const int ld = cx->n_max | 1;
     const size_t smem_store = collide_smem<T>(nthr) + (size_t)ld * ld * sizeof(T) +
                               (cx->tracer ? (size_t)nthr * sizeof(double) : 0);
-    const bool store = sizeof(T) == 4 && cx->dv_matrix && smem_store <= (size_t)cx->smem_optin;
+    // FP64: the matrices live in the workspace (when it holds them), not in shared memory
+    const bool store = cx->dv_matrix && (sizeof(T) == 4 ? smem_store <= (size_t)cx->smem_optin : cx->dvg != nullptr);
     A.dv_ld = ld;
+    A.dvg = cx->dvg;
     // a fragmentation ramp in any disk, or the tracer, selects the kernel variant with its branch
     auto go = [&](auto kernel, size_t bytes) {
         kernel<<<(unsigned)cx->C, nthr, bytes, cx->stream>>>(A);
@@ -1033,13 +1037,12 @@ static cudaError_t collide_impl(mcd_ctx *cx, int from_state, double t_end)
         return cudaGetLastError();
     };
     const size_t tq = cx->tracer ? (size_t)nthr * sizeof(double) : 0;  // the tracer's shared-memory copy
-    if constexpr (sizeof(T) == 4)
-        if (store) {
-            const size_t b = smem_store > smem + tq ? smem_store : smem + tq;
-            if (cx->tracer)
-                return cx->ramp ? go(k_collide<T, true, true, true>, b) : go(k_collide<T, true, false, true>, b);
-            return cx->ramp ? go(k_collide<T, true, true, false>, b) : go(k_collide<T, true, false, false>, b);
-        }
+    if (store) {
+        const size_t b = sizeof(T) == 4 ? (smem_store > smem + tq ? smem_store : smem + tq) : smem + tq;
+        if (cx->tracer)
+            return cx->ramp ? go(k_collide<T, true, true, true>, b) : go(k_collide<T, true, false, true>, b);
+        return cx->ramp ? go(k_collide<T, true, true, false>, b) : go(k_collide<T, true, false, false>, b);
+    }
     if (cx->tracer)
         return cx->ramp ? go(k_collide<T, false, true, true>, smem + tq) : go(k_collide<T, false, false, true>, smem + tq);
     return cx->ramp ? go(k_collide<T, false, true, false>, smem) : go(k_collide<T, false, false, false>, smem);
@@ -1071,6 +1074,10 @@ static cudaError_t prepare_impl(mcd_ctx *c)
                                              (size_t)kMaxCell * sizeof(double)));  // + the tracer's copy
     c->smem_optin = 0;
     if constexpr (sizeof(T) != 4) {
+        // the FP64 stored-matrix variants keep their matrices in global memory
+        if (e == cudaSuccess)
+            e = set_smem<T, true>((int)((need > kExclusiveSmem ? need : kExclusiveSmem) +
+                                        (size_t)kMaxCell * sizeof(double)));
         return e;
     } else {
         if (e != cudaSuccess) return e;

@@ -250,6 +250,7 @@ struct mcd_ctx {
     double *cell_b = nullptr;  // 6 per cell: r_lo r_hi z_lo z_hi r_c z_c
     double *cell_V = nullptr;
     unsigned char *cellk = nullptr;  // per-cell constants, kCellKBytes each
+    double *dvg = nullptr;           // FP64 path: stored dv matrices, ld x ld per cell (null: recompute)
 
     int64_t *cell_events = nullptr;
     uint32_t *cell_cost = nullptr;

@@ -448,13 +448,14 @@ def test_graph_replay_equals_direct_launches(prec):
     b.close()
 
 
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("grid,reb", [((8, 4, 30), 0), ((4, 2, 57), 7), ((1, 1, 200), 0), ((2, 2, 224), 13)])
-def test_dv_matrix_equals_recompute(grid, reb):
-    """Collide with each cell's dv matrix kept in shared memory reaches the same
-    bits as the path that recomputes row i at every event.  Mid-run state, so
-    sticking, erosion and fragmentation all occur; reb > 0 also runs the full
-    rebuilds from stored entries; 224 particles per cell is the largest matrix
-    that fits."""
+def test_dv_matrix_equals_recompute(grid, reb, prec):
+    """Collide with each cell's dv matrix kept (mixed: in shared memory; FP64:
+    in the workspace) reaches the same bits as the path that recomputes row i
+    at every event.  Mid-run state, so sticking, erosion and fragmentation all
+    occur; reb > 0 also runs the full rebuilds from stored entries; 224
+    particles per cell is the largest matrix that fits in shared memory."""
     P = W.benchmark_disk()
     N = grid[0] * grid[1] * grid[2]
     m, r, z = W.midrun_state(P, N, seed=3)
@@ -463,7 +464,7 @@ def test_dv_matrix_equals_recompute(grid, reb):
     r, z = r2, z * (r2 / r) ** 1.25
     out = []
     for mat in (1, 0):
-        d = _make_ctx(P, grid, seed=4, prec=mcd.MCD_MIXED)
+        d = _make_ctx(P, grid, seed=4, prec=prec)
         p = d.particles()
         mcd.mcd_set_particles(d.ctx, 0, m, p["M"], r, z, p["id"])
         for key, v in ((mcd.MCD_OPT_DV_MATRIX, mat), (mcd.MCD_OPT_REBUILD_EVERY, reb), (mcd.MCD_OPT_DUMP_R, 1)):
