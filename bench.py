@@ -51,32 +51,43 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples during the timed region."""
+    """nvidia-smi clock/throttle samples during the timed region: the sampler
+    starts first and the region waits (up to 3 s) for its first sample; only
+    samples stamped between start() and stop() count (the nearest one when
+    the region is shorter than the sampling period)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 20
 
     def __init__(self, index: int):
         self.index, self.rows, self.proc = index, [], None
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            deadline = time.perf_counter() + 3.0
+            while not self.rows and time.perf_counter() < deadline:
+                time.sleep(0.005)
         except Exception:
             self.proc = None
+        self.t0 = time.perf_counter()
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(",")])
+            self.rows.append((time.perf_counter(), [x.strip() for x in line.split(",")]))
 
     def __exit__(self, *a):
+        self.t1 = time.perf_counter()
         if self.proc:
+            time.sleep(2e-3 * self.PERIOD_MS)  # one more sample past the end
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -84,13 +95,17 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        rows = [r for t, r in self.rows if self.t0 is not None and self.t0 <= t <= self.t1]
+        if not rows and self.rows and self.t0 is not None:  # region shorter than the period: the nearest sample
+            rows = [min(self.rows, key=lambda tr: abs(tr[0] - 0.5 * (self.t0 + self.t1)))[1]]
+        sm = [float(r[1]) for r in rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        reasons = sorted({names[k] for r in self.rows if len(r) > 8 for k in range(4)
+        reasons = sorted({names[k] for r in rows if len(r) > 8 for k in range(4)
                           if r[5 + k].lower().startswith("active")})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(sm)}
+                "reasons": reasons, "samples": len(sm),
+                "window_ms": 1e3 * (self.t1 - self.t0) if self.t0 is not None and self.t1 else None}
 
 
 def measured_traffic(name: str):
@@ -150,8 +165,15 @@ def make_state(args, ctx_or_none, rank):
 
 
 def cpu_model() -> str:
-    """The host CPU as the kernel names it (model name, else the architecture)."""
+    """The host CPU: lscpu's model name, else /proc/cpuinfo's, else the architecture."""
     import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
