@@ -873,3 +873,18 @@ def test_adaptive_run_equals_fixed_steps_of_its_dts():
     for key in ("m", "r", "z", "id"):
         assert np.array_equal(getattr(a, key), getattr(b, key)), key
     assert a.events == b.events and a.accreted == b.accreted
+
+
+# ---- the paper's Benchmark table ---------------------------------------------
+def test_benchmark_disk_is_the_papers_table():
+    """The workload's disk carries the Benchmark section's parameter table
+    (tests/golden/benchmark_table.txt), converted to CGS."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "benchmark_table.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 7
+    P = W.benchmark_disk()
+    for name, printed, unit, cgs in rows:
+        assert P[name] == float(cgs), name
+        scale = {"m/s": 100.0}.get(unit, 1.0)
+        assert float(printed) * scale == float(cgs), name
