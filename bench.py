@@ -412,13 +412,61 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_batched(args):
+    """The 64-disk batch (workloads.batched_disks) in one context: mixed path,
+    one mid-run state per disk, whole-batch events/s over timed steps.  A
+    measurement of that configuration, not the benchmark line."""
+    import torch
+    from paper_2507_21239_gb300 import build as B, mcd, workloads as W
+    torch.cuda.set_device(0)
+    B.build()
+    disks = W.batched_disks()
+    params = [x["params"] for x in disks]
+    grids = [(x["n_r"], x["n_z"], x["per_cell"]) for x in disks]
+    stream = torch.cuda.Stream()
+    flush = torch.empty(max(args.flush_mb, 1) << 20, dtype=torch.uint8, device="cuda")
+    d = mcd.Disk(params, grids, seed=0, prec="mixed", stream=stream)
+    for k, g in enumerate(grids):
+        m, r, z = W.midrun_state(params[k], g[0] * g[1] * g[2], seed=k)
+        p = d.particles(k)
+        mcd.mcd_set_particles(d.ctx, k, m, p["M"], r, z, p["id"])
+    dt = args.dt_yr * W.YR
+    mcd.mcd_trace(d.ctx, True)
+    for _ in range(args.warmup):
+        mcd.mcd_step(d.ctx, dt)
+    torch.cuda.synchronize()
+    events = lambda: sum(d.stats(k).events for k in range(len(disks)))
+    ev0, l0 = events(), mcd.mcd_get_launch_count(d.ctx)
+    with ClockSampler(0) as clk:
+        times, phases = timed_steps(mcd, d, dt, args.steps, stream, flush)
+    torch.cuda.synchronize()
+    ev = events() - ev0
+    launches = mcd.mcd_get_launch_count(d.ctx) - l0
+    status = mcd.mcd_sync(d.ctx)
+    total_ms = float(times.sum())
+    ph = phases.mean(axis=0)
+    n = sum(g[0] * g[1] * g[2] for g in grids)
+    out = {"metric": METRIC, "value": ev / (total_ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "dtype": "f32+f64 (mixed)", "data": "synthetic", "status": mcd.mcd_strerror(status),
+           "config": {"workload": "batched64", "disks": len(disks), "particles": n,
+                      "cells": sum(g[0] * g[1] for g in grids), "dt_yr": args.dt_yr,
+                      "state": "workloads.midrun_state per disk (seed = disk)"},
+           "events_per_step": ev / args.steps,
+           "phases_ms": {"regrid": ph[0], "order": ph[1], "collide": ph[2], "transport": ph[3]},
+           "gpu_launches": launches, "clocks": clk.summary()}
+    d.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", default="disk2d_256x16x200")
+    ap.add_argument("--workload", default="disk2d_256x16x200",
+                    help="a workloads.WORKLOADS name, or batched64 (the 64-disk batch, mixed path only)")
     ap.add_argument("--dt-yr", dest="dt_yr", type=float, default=1.0)
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--e2e-steps", type=int, default=10)
@@ -430,6 +478,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched64":
+        run_batched(args)
     else:
         run_ours(args)
 
