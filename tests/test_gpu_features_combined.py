@@ -90,3 +90,30 @@ def test_mixed_batched_feature_subsets():
         assert np.all((tq >= -1e-12) & (tq <= 1 + 1e-12)), k
         assert 0.0 < (x["M"][alive] * tq[alive]).sum() / x["M"][alive].sum() < 1.0
     d.close()
+
+
+def test_emptied_disk_latches_eempty_while_others_step():
+    """A disk whose particles are all removed latches MCD_EEMPTY at the next
+    regrid; the other disk of the context keeps stepping and conserving mass,
+    with the adaptive step too (the empty disk asks for nothing)."""
+    P = W.benchmark_disk()
+    grids = [(8, 2, 20), (4, 2, 10)]
+    d = mcd.Disk([P, P], grids, seed=1, prec=mcd.MCD_MIXED)
+    p = d.particles(1)
+    mcd.mcd_set_particles(d.ctx, 1, p["m"], p["M"], np.full(p["r"].size, np.inf), p["z"], p["id"])
+    mcd.mcd_regrid(d.ctx)
+    assert mcd.mcd_sync(d.ctx) == mcd.MCD_EEMPTY
+    assert d.stats(1).n_alive == 0 and d.stats(1).status == mcd.MCD_EEMPTY
+    m0 = d.particles(0)["M"].sum()
+    m, r, z = W.midrun_state(P, 8 * 2 * 20, seed=2)
+    q = d.particles(0)
+    mcd.mcd_set_particles(d.ctx, 0, m, q["M"], r, z, q["id"])
+    for dt in (YR, 0.0, 0.0):
+        d.step(dt)
+    assert mcd.mcd_sync(d.ctx) == mcd.MCD_EEMPTY  # latched
+    x, st = d.particles(0), d.stats(0)
+    alive = np.isfinite(x["r"])
+    assert st.events > 0 and st.n_alive == alive.sum() > 0
+    assert abs(x["M"][alive].sum() + st.accreted_mass - m0) <= 1e-12 * m0
+    assert d.stats(1).events == 0 and d.stats(1).accreted_mass == 0.0
+    d.close()
