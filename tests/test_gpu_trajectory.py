@@ -3,8 +3,9 @@ disk evolutions.
 
 The mixed path evaluates rates in FP32, so its event sequence departs from the
 oracle's after the first rounding-sensitive choice; what must agree is the
-outcome in distribution.  On the 16 x 4 x 100 Benchmark-table disk, 16 seeds
-evolve for 2,000 yr (through the growth and fragmentation phases) on the GPU
+outcome in distribution.  On the 16 x 4 x 100 Benchmark-table disk, with the
+power-law gas and with the gap-and-bump gas table (dust piles up at the
+pressure bump), 16 seeds evolve for 2,000 yr (through the growth and fragmentation phases) on the GPU
 (one batched context, disk d keyed by (seed, d) like the oracle's runs) and in
 the oracle.  Per logarithmic radial bin (16 bins over r_in .. r_out):
 
@@ -50,9 +51,11 @@ class _Orc:
         self.m, self.M, self.r = m, M, r
 
 
-def _runs():
+def _runs(gas):
     wl = W.WORKLOADS["disk2d_16x4x100"]
     P, grid = wl["params"], (wl["n_r"], wl["n_z"], wl["per_cell"])
+    if gas == "gap_bump_table":  # dust piles up at the pressure bump
+        P = dict(P, gas_table=W.gap_bump_gas_table(P, noise=0.01, seed=3))
     edges = P["r_in"] * np.geomspace(1.0, P["r_out"] / P["r_in"], 17)
     oracle.lib()  # built before the workers load it
     # the oracle runs in spawned single-threaded workers while the GPU runs
@@ -74,9 +77,9 @@ def _runs():
     return edges, gpu, orc
 
 
-@pytest.fixture(scope="module")
-def runs():
-    return _runs()
+@pytest.fixture(scope="module", params=["power_law", "gap_bump_table"])
+def runs(request):
+    return _runs(request.param)
 
 
 def test_mass_conserved(runs):
