@@ -888,3 +888,46 @@ def test_benchmark_disk_is_the_papers_table():
         assert P[name] == float(cgs), name
         scale = {"m/s": 100.0}.get(unit, 1.0)
         assert float(printed) * scale == float(cgs), name
+
+
+def test_adaptive_dt_in_a_tabulated_disk():
+    """The adaptive step with a gas table: the same numpy statement from the
+    pinned particle and gas functions, now reading the tabulated gas; the
+    table changes the step."""
+    P = dict(W.benchmark_disk(), gas_table=_bump_table())
+    N, grid = 400, (20, 2)
+    m, r, z = W.midrun_state(P, N, seed=6)
+    s = oracle.DiskState(m, np.full(N, 1e26), r, z, np.arange(N, dtype=np.uint32))
+    _, _, off, cb, _, _ = oracle.regrid(P, *grid, s)
+    v = []
+    for k in range(N):
+        St = oracle.particle(P, s.r[k], s.z[k], s.m[k])[1][0]
+        eta = oracle.gas(P, s.r[k], s.z[k])["etavk"][0]
+        v.append(abs(2 * eta * St / (1 + St**2)))
+    dr = (cb[:, 1] - cb[:, 0])[np.diff(off) > 0].min()
+    got = oracle.adaptive_dt(P, off, cb, s, 1e30)
+    assert got == pytest.approx(0.5 * dr / max(v), rel=1e-13)
+    P0 = W.benchmark_disk()
+    assert abs(oracle.adaptive_dt(P0, off, cb, s, 1e30) / got - 1) > 1e-3
+
+
+def test_adaptive_run_with_tracer_equals_fixed_steps():
+    """The tracer rides through an adaptive run exactly as through fixed-step
+    runs of the steps it chose."""
+    P = W.benchmark_disk()
+    N, grid, seed, dt_max = 400, (20, 2), 9, 1e4 * YR
+    m, r, z = W.midrun_state(P, N, seed=11)
+    ids = np.arange(N, dtype=np.uint32)
+    a = oracle.DiskState(m.copy(), np.full(N, 1e26), r.copy(), z.copy(), ids.copy())
+    b = oracle.DiskState(m.copy(), np.full(N, 1e26), r.copy(), z.copy(), ids.copy())
+    a.q = 0.2 + 0.6 * (ids % 3) / 2.0
+    b.q = a.q.copy()
+    dts = np.zeros(3)
+    assert oracle.run(P, *grid, a, 0.0, 0.0, 0, 3, seed, dt_max=dt_max, dts=dts) == 0
+    t = 0.0
+    for k in range(3):
+        assert oracle.run(P, *grid, b, t, dts[k], k, 1, seed) == 0
+        t += dts[k]
+    for key in ("m", "r", "z", "id", "q"):
+        assert np.array_equal(getattr(a, key), getattr(b, key)), key
+    assert not np.array_equal(a.q, 0.2 + 0.6 * (a.id % 3) / 2.0)  # collisions mixed it
