@@ -342,6 +342,23 @@ class Disk:
         mcd_get_particles(self.ctx, disk, out["m"], out["M"], out["r"], out["z"], out["id"], MCD_HOST)
         return out
 
+    def particles_device(self, disk: int = 0) -> dict:
+        """The disk's particles in cell order as CUDA tensors (m, M, r, z float64;
+        id int32 holding the uint32 ids), copied on the device; the current torch
+        stream is ordered after the copy."""
+        import torch
+        g = self.grids[disk] if isinstance(self.grids[0], (tuple, list)) else self.grids
+        n = int(g[0]) * int(g[1]) * int(g[2])
+        dev = self.workspace.device
+        out = {k: torch.empty(n, dtype=torch.float64, device=dev) for k in ("m", "M", "r", "z")}
+        out["id"] = torch.empty(n, dtype=torch.int32, device=dev)
+        if self.stream is not None:
+            self.stream.wait_stream(torch.cuda.current_stream())  # the fresh tensors before the copy
+        mcd_get_particles(self.ctx, disk, out["m"], out["M"], out["r"], out["z"], out["id"], MCD_DEVICE)
+        if self.stream is not None:
+            torch.cuda.current_stream().wait_stream(self.stream)
+        return out
+
     def stats(self, disk: int = 0) -> mcd_stats:
         return mcd_get_stats(self.ctx, disk)
 

@@ -117,3 +117,17 @@ def test_emptied_disk_latches_eempty_while_others_step():
     assert abs(x["M"][alive].sum() + st.accreted_mass - m0) <= 1e-12 * m0
     assert d.stats(1).events == 0 and d.stats(1).accreted_mass == 0.0
     d.close()
+
+
+def test_particles_as_device_tensors():
+    """Disk.particles_device gives the host copy's values as CUDA tensors, on a
+    private stream too."""
+    P = W.benchmark_disk()
+    for stream in (None, torch.cuda.Stream()):
+        d = mcd.Disk(P, (8, 2, 25), seed=2, prec=mcd.MCD_MIXED, stream=stream)
+        d.step(YR)
+        x, t = d.particles(), d.particles_device()
+        for k in ("m", "M", "r", "z"):
+            assert t[k].is_cuda and np.array_equal(t[k].cpu().numpy(), x[k]), k
+        assert np.array_equal(t["id"].cpu().numpy().view(np.uint32), x["id"])
+        d.close()
