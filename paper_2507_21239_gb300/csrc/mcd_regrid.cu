@@ -269,18 +269,37 @@ __global__ void __launch_bounds__(kRadixThreads, 2) k_radix_scatter(const DiskDe
     }
 }
 
+// the first position of each disk's sorted keys that holds +inf (a removed
+// particle): one warp per disk, a 32-way search (each round narrows [lo, hi)
+// to one of 32 sub-ranges with one load per lane), so the dependent loads are
+// log32 of the disk's size rather than log2
 __global__ void k_count_alive(const DiskDev *disks, int nd, const uint64_t *key, int64_t *n_alive, int32_t *status)
 {
-    int d = blockIdx.x * blockDim.x + threadIdx.x;
+    const int d = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (d >= nd) return;
     const DiskDev D = disks[d];
-    int64_t lo = 0, hi = D.n0;  // first position whose key is +inf
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (key[D.p_off + mid] < kInfKey) lo = mid + 1; else hi = mid;
+    const uint64_t *k = key + D.p_off;
+    int64_t lo = 0, hi = D.n0;  // the answer lies in [lo, hi]: keys below lo are finite, from hi on +inf
+    while (hi - lo > 0) {
+        // lane l probes position lo + (l + 1) * ceil((hi - lo) / 32) - 1 (the last of its sub-range)
+        const int64_t step = (hi - lo + 31) >> 5;
+        const int64_t p = lo + (int64_t)(lane + 1) * step - 1;
+        const bool inf = p < hi && !(k[p] < kInfKey);
+        const unsigned b = __ballot_sync(0xffffffffu, inf);
+        if (b == 0u) {
+            lo += ((hi - lo) / step) * step;  // every probed key finite: one past the last probe below hi
+        } else {
+            const int f = __ffs(b) - 1;  // the first sub-range whose last key is +inf
+            const int64_t nlo = lo + (int64_t)f * step, nhi = lo + (int64_t)(f + 1) * step - 1;
+            lo = nlo;
+            hi = nhi;  // the answer is in [nlo, nhi]: position nhi is +inf
+            if (step == 1) break;
+        }
     }
-    n_alive[d] = lo;
-    if (lo == 0 && D.n0 > 0) atomicOr(status, kStEmpty);
+    if (lane == 0) {
+        n_alive[d] = lo;
+        if (lo == 0 && D.n0 > 0) atomicOr(status, kStEmpty);
+    }
 }
 
 // a zone element in shared memory: (z key lo, z key hi, id, source slot)
@@ -635,7 +654,7 @@ cudaError_t launch_regrid(mcd_ctx *c)
             c->scan_part);
     }
     // kRadixPasses is even: the sorted keys are back in buffer 0
-    k_count_alive<<<(c->n_disks + 63) / 64, 64, 0, st>>>(c->d_disks, c->n_disks, c->key[0], c->n_alive, c->status);
+    k_count_alive<<<(c->n_disks + 7) / 8, 256, 0, st>>>(c->d_disks, c->n_disks, c->key[0], c->n_alive, c->status);
     ZoneArgs A;
     A.params = c->d_params;
     A.disks = c->d_disks;
