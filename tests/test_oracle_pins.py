@@ -931,3 +931,39 @@ def test_adaptive_run_with_tracer_equals_fixed_steps():
     for key in ("m", "r", "z", "id", "q"):
         assert np.array_equal(getattr(a, key), getattr(b, key)), key
     assert not np.array_equal(a.q, 0.2 + 0.6 * (a.id % 3) / 2.0)  # collisions mixed it
+
+
+# ---- turbulent relative velocity: the textbook limits of the closed forms ----
+@pytest.mark.parametrize("ratio", [0.0, 0.3])
+def test_turbulence_small_grain_limit(ratio):
+    """Grains far below the Kolmogorov scale (St << St_eta = Re^-1/2) move
+    relative to each other at V_g Re^{1/4} |St_1 - St_2|, the classical
+    small-eddy result that regime I of Ormel & Cuzzi (2007) reduces to."""
+    P = W.benchmark_disk(dv_flags=2)
+    r = 5 * AU
+    g = oracle.gas(P, r, 0.0)
+    Se, vg2 = g["St_eta"][0], g["vg2"][0]
+    St1 = 1e-3 * Se
+    m1 = _mass_for_St(P, r, 0.0, St1)
+    m2 = _mass_for_St(P, r, 0.0, max(ratio * St1, 1e-12 * St1))
+    S1 = oracle.particle(P, r, 0.0, m1)[1][0]
+    S2 = oracle.particle(P, r, 0.0, m2)[1][0]
+    dv = oracle.pairs(P, r, 0.0, m1, m2)["dv"][0]
+    ref = np.sqrt(vg2 / Se) * abs(S1 - S2)  # V_g Re^{1/4} |dSt|, Re^{1/2} = 1/St_eta
+    assert S2 < S1 and abs(dv / ref - 1) < 3 * S1 / Se  # the limit's leading correction is O(St/St_eta)
+
+
+@pytest.mark.parametrize("St1,St2", [(3e3, 1e3), (1e4, 1e4)])
+def test_turbulence_heavy_grain_limit(St1, St2):
+    """Grains much heavier than the largest eddies (St >> 1) keep relative
+    velocities dv^2 -> V_g^2 (1/St_1 + 1/St_2) (Volk et al. 1980), the limit of
+    regime III."""
+    P = W.benchmark_disk(dv_flags=2)
+    r = 5 * AU
+    vg2 = oracle.gas(P, r, 0.0)["vg2"][0]
+    m1, m2 = _mass_for_St(P, r, 0.0, St1), _mass_for_St(P, r, 0.0, St2)
+    S1 = oracle.particle(P, r, 0.0, m1)[1][0]
+    S2 = oracle.particle(P, r, 0.0, m2)[1][0]
+    dv = oracle.pairs(P, r, 0.0, m1, m2)["dv"][0]
+    ref = vg2 * (1 / S1 + 1 / S2)
+    assert abs(dv**2 / ref - 1) < 2.0 / min(S1, S2)  # the closed form's 1/(1+St) against 1/St
