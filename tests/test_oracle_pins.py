@@ -967,3 +967,26 @@ def test_turbulence_heavy_grain_limit(St1, St2):
     dv = oracle.pairs(P, r, 0.0, m1, m2)["dv"][0]
     ref = vg2 * (1 / S1 + 1 / S2)
     assert abs(dv**2 / ref - 1) < 2.0 / min(S1, S2)  # the closed form's 1/(1+St) against 1/St
+
+
+@pytest.mark.parametrize("dm", [0.0, 1e-3, 1e-1])
+def test_grouping_keeps_the_mass_growth_rate(dm):
+    """Zsom & Dullemond grouping: swarm i meets dm m_i / m_j particles of a much
+    lighter swarm j in one event, at a rate divided by that number.  The rate
+    times the mass gained is therefore K_ij M_j / V for every pair, whatever dm:
+    grouping changes the noise of growth, not its mean."""
+    P = W.benchmark_disk(dm_group=dm)
+    rc, zc, V = 1.2 * AU, 1e11, 1e39
+    rng = np.random.default_rng(3)
+    n = 12
+    m = 10.0 ** rng.uniform(-11, 2, n)
+    M = 10.0 ** rng.uniform(24, 27, n)
+    rate, R = oracle.rate_matrix(P, rc, zc, V, m, M)
+    assert np.allclose(rate.sum(axis=1), R, rtol=1e-13, atol=0)
+    for i in range(n):
+        K = oracle.pairs(P, rc, zc, np.full(n, m[i]), m)["K"]
+        gain = np.maximum(m, dm * m[i])
+        got = rate[i] * gain
+        assert np.allclose(got, K * M / V, rtol=1e-13, atol=0), i
+    if dm > 0:  # grouping does act here: some partners are below dm m_i
+        assert np.any(m[None, :] < dm * m[:, None])
