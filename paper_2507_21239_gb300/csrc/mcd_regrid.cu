@@ -313,6 +313,7 @@ __device__ __forceinline__ bool zless(const uint4 &a, const uint4 &b)
 constexpr int kZoneThreads = 512;  // two zones per SM
 constexpr int kZoneItems = 8;      // radix path: elements per lane, zones up to 16 x 32 x 8 = 4,096
 constexpr int kZoneRadixMax = (kZoneThreads / 32) * 32 * kZoneItems;
+constexpr int kTieRun = 64;  // longest run of equal heights the radix path orders by id in place
 
 // digit of element e in pass p: the first id_passes take the id's bytes, the
 // next eight the z key's (least significant first)
@@ -439,25 +440,64 @@ __global__ void __launch_bounds__(kZoneThreads, 2) k_zone(ZoneArgs A)
     const uint64_t *rk = A.rkey + D.p_off;
 
     // (1) load this zone's (z, id, source) triples
-    for (int64_t q = threadIdx.x; q < nk; q += blockDim.x) {
-        uint32_t src = A.rsrc[D.p_off + zs + q];
-        if ((int64_t)src >= D.n0) {  // ids were not a permutation
-            atomicOr(A.status, kStBadCell);
-            src = 0;
+    auto load = [&]() {
+        for (int64_t q = threadIdx.x; q < nk; q += blockDim.x) {
+            uint32_t src = A.rsrc[D.p_off + zs + q];
+            if ((int64_t)src >= D.n0) {  // ids were not a permutation
+                atomicOr(A.status, kStBadCell);
+                src = 0;
+            }
+            int64_t gs = D.p_off + src;
+            double zz = A.z0[gs];
+            if (isnan(zz)) {
+                atomicOr(A.status, kStNaN);
+                zz = INFINITY;
+            }
+            const uint64_t kz = order_key(zz);
+            el[q] = make_uint4((uint32_t)kz, (uint32_t)(kz >> 32), A.id0[gs], src);
         }
-        int64_t gs = D.p_off + src;
-        double zz = A.z0[gs];
-        if (isnan(zz)) {
-            atomicOr(A.status, kStNaN);
-            zz = INFINITY;
-        }
-        const uint64_t kz = order_key(zz);
-        el[q] = make_uint4((uint32_t)kz, (uint32_t)(kz >> 32), A.id0[gs], src);
-    }
-    __syncthreads();
+        __syncthreads();
+    };
+    load();
     // (2) sort by (z, id)
     if (A.radix) {
-        el = zone_radix(el, el + A.zcap, (int)nk, A.id_passes, reinterpret_cast<unsigned char *>(el + 2 * A.zcap));
+        // The z passes alone: a stable sort keeps equal z keys in their input
+        // (r) order, so each run of equal keys is then put in id order by the
+        // thread at its start (runs are disjoint, and swapping inside a run
+        // leaves every key of it unchanged).  A run longer than kTieRun redoes
+        // the sort with the id passes first.
+        uint4 *const base = el;
+        unsigned char *const scratch = reinterpret_cast<unsigned char *>(base + 2 * A.zcap);
+        el = zone_radix(base, base + A.zcap, (int)nk, 0, scratch);
+        __shared__ int long_run;
+        if (threadIdx.x == 0) long_run = 0;
+        __syncthreads();
+        const int n32 = (int)nk;
+        for (int q = threadIdx.x; q + 1 < n32; q += blockDim.x) {
+            const uint64_t kq = el_key(el[q]);
+            if (el_key(el[q + 1]) != kq || (q > 0 && el_key(el[q - 1]) == kq)) continue;
+            int e = q + 1;
+            while (e + 1 < n32 && el_key(el[e + 1]) == kq) ++e;
+            if (e - q + 1 > kTieRun) {
+                long_run = 1;
+                continue;
+            }
+            for (int i = q + 1; i <= e; ++i) {  // insertion sort of el[q..e] by id
+                const uint4 x = el[i];
+                int j = i - 1;
+                while (j >= q && el[j].z > x.z) {
+                    el[j + 1] = el[j];
+                    --j;
+                }
+                el[j + 1] = x;
+            }
+        }
+        __syncthreads();
+        if (long_run) {
+            el = base;
+            load();
+            el = zone_radix(base, base + A.zcap, (int)nk, A.id_passes, scratch);
+        }
     } else {
         // (2) bitonic sort by (z, id); every compare ascending, i < j, j < nk
         //     (32-bit indices; strides are powers of two, so / and % are shifts).

@@ -176,6 +176,48 @@ def test_regrid_bit_exact(grids, dead):
     d.close()
 
 
+@pytest.mark.parametrize("kind", ["all_equal", "three_levels", "short_runs"])
+def test_regrid_equal_heights_bit_exact(kind):
+    """Heights that repeat within a zone: every height equal, three distinct
+    heights (runs longer than the in-place tie fix-up takes), and heights
+    rounded so that runs of equal heights stay short.  The cells' (z, id)
+    order, counts and bounds equal the oracle's."""
+    P = W.benchmark_disk()
+    grid = (4, 8, 100)
+    N = grid[0] * grid[1] * grid[2]
+    rng = np.random.default_rng(21)
+    r = rng.uniform(P["r_in"], 0.3 * P["r_out"], N)
+    if kind == "all_equal":
+        z = np.zeros(N)
+    elif kind == "three_levels":
+        z = rng.choice([-1e11, 0.0, 2e11], N)
+    else:
+        z = np.round(rng.normal(0, 1, N) * 30) * 1e10  # ~60 distinct heights per zone of 800
+    z[::97 if kind == "short_runs" else 7] = -0.0  # negative zero orders with +0 (short_runs: runs stay short)
+    m = W.random_masses(N, seed=22, lo=1e-11, hi=1e-2)
+    M = np.full(N, 1e26)
+    ids = rng.permutation(N).astype(np.uint32)
+    d = _make_ctx(P, grid)
+    mcd.mcd_set_particles(d.ctx, 0, m, M, r, z, ids)
+    mcd.mcd_regrid(d.ctx)
+    assert mcd.mcd_sync(d.ctx) == mcd.MCD_OK
+    s = oracle.DiskState(m, M, r, z, ids)
+    st, _, off, cb, cv, na = oracle.regrid(P, grid[0], grid[1], s)
+    assert st == 0
+    got = d.particles()
+    assert np.array_equal(got["id"], s.id)
+    for key in ("m", "M", "r", "z"):
+        assert np.array_equal(got[key].view(np.uint64), getattr(s, key).view(np.uint64)), key
+    goff = np.zeros(grid[0] * grid[1] + 1, np.int64)
+    gb = np.zeros((grid[0] * grid[1], 6))
+    mcd.mcd_get_cells(d.ctx, 0, goff, gb, None)
+    assert np.array_equal(goff, off)
+    n_cell = np.diff(off)
+    exact = n_cell != 1
+    assert np.array_equal(gb[exact].view(np.uint64), cb[exact].view(np.uint64))
+    d.close()
+
+
 # ----------------------------------------------------------------- transport ---
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("flags", [3, 1, 2, 2 | 4])
