@@ -337,10 +337,10 @@ int mcd_rate_probe(const mcd_disk_params *p, int32_t prec, double r_c, double z_
 /*
  * Regrid of one disk that allocates nothing (the paper has no counterpart;
  * this is a service entry point).  For callers that cannot call cudaMalloc:
- * code that runs inside another framework's memory pool or arena, code that
- * runs inside a caller's CUDA-graph capture or real-time loop where an
- * allocation would stall or break it, and embedded users with a fixed memory
- * budget.  It does what mcd_regrid does for one disk, without a context: the
+ * code that runs inside another framework's memory pool or arena (which owns
+ * every allocation), real-time loops where an allocation would stall, and
+ * embedded users with a fixed memory budget.  It does what mcd_regrid does
+ * for one disk, without a context: the
  * caller passes the particle arrays (n_r * n_z * per_cell of each, device
  * pointers; ids a permutation of 0..count-1, r = +inf for removed particles)
  * and receives the arrays in cell order (m_out .. id_out), each cell's first
@@ -354,10 +354,12 @@ int mcd_rate_probe(const mcd_disk_params *p, int32_t prec, double r_c, double z_
  * fixed device array of about 2.1 MB that every GPU loading the library holds
  * until the process exits; hence at most MCD_NOALLOC_MAX_PARTICLES particles
  * (MCD_EINVAL beyond, and when one radial zone holds more than 14,336).  The
- * first call on a device looks the array up; make it before any stream
- * capture.  All calls share the array: calls that overlap on the GPU race on
- * it and must be serialised by the caller.  It calls no cudaMalloc, cudaFree or
- * allocating library routine.
+ * first call on a device looks the array's device address up; make it before
+ * any stream capture.  All calls share the array and it keeps the previous
+ * call's contents (the status bits are cleared at the start of each call):
+ * calls that overlap on the GPU race on it and must be serialised by the
+ * caller.  It calls no cudaMalloc, cudaFree or allocating library routine;
+ * its disk tables reach the device as kernel arguments, not host copies.
  */
 #define MCD_NOALLOC_MAX_PARTICLES 65536
 int mcd_regrid_noalloc(const mcd_disk_params *p, const mcd_grid *g, const double *m, const double *M,

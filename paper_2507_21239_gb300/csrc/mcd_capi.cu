@@ -13,8 +13,6 @@ using namespace mcd;
 
 namespace {
 
-constexpr int64_t kZoneCap = 14336;  // (z, id, src) triples of one radial zone in shared memory
-
 struct Carver {
     char *base;
     size_t off = 0;
@@ -241,6 +239,11 @@ int mcd_init_disk(mcd_ctx **out, const mcd_disk_params *p, const mcd_grid *g, in
     c->Z = S.Z;
     c->n_tiles = S.T;
     c->n_max = S.n_max;
+    for (int32_t d = 0; d < n_disks; ++d) {
+        const int64_t zc = (int64_t)g[d].n_z * g[d].per_cell;
+        c->zone_max = c->zone_max > zc ? c->zone_max : zc;
+        c->n0_max = c->n0_max > (int64_t)g[d].n_r * zc ? c->n0_max : (int64_t)g[d].n_r * zc;
+    }
     carve(c, ws, S, n_disks, prec);
     double *d_Mswarm = c->d_Mswarm;
 

@@ -1049,8 +1049,6 @@ static cudaError_t collide_impl(mcd_ctx *cx, int from_state, double t_end)
 }
 
 // the dynamic shared memory each variant may request; for the stored-matrix
-// variant, what the device lets a block opt in to beyond its static part
-// the dynamic shared memory each variant may request; for the stored-matrix
 // variants, what the device lets a block opt in to beyond its static part
 template <class T, bool STORE>
 static cudaError_t set_smem(int bytes)

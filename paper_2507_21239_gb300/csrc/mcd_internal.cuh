@@ -213,6 +213,10 @@ constexpr int kRadixBins = 256, kRadixPasses = 8;
 // largest cell population the collide kernel takes (one thread per swarm)
 constexpr int kMaxCell = 512;
 
+// largest radial zone the regrid sorts in shared memory: (z, id, source)
+// elements of 16 bytes, 224 KB
+constexpr int64_t kZoneCap = 14336;
+
 // bytes reserved per cell for its gas/drag constants
 constexpr int kCellKBytes = 384;
 
@@ -228,6 +232,7 @@ struct mcd_ctx {
     std::vector<mcd::DiskDev> hd;
     int64_t N = 0, C = 0, Z = 0, n_tiles = 0;
     int32_t n_max = 0;  // largest possible cell population
+    int64_t zone_max = 0, n0_max = 0;  // largest radial zone (n_z * per_cell) and disk (particles)
 
     mcd_disk_params *d_params = nullptr;
     mcd::DiskDev *d_disks = nullptr;

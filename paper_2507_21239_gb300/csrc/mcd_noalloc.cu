@@ -3,12 +3,12 @@
 //
 // Some callers cannot call cudaMalloc: code running inside another
 // framework's memory pool or arena (which owns every allocation and forbids
-// side allocations), plugins that run inside a caller's CUDA-graph capture or
-// real-time loop where allocation would stall or break the capture, and
+// side allocations), real-time loops where an allocation would stall, and
 // embedded users with a fixed memory budget.  This entry point takes the
 // caller's input and output arrays and keeps its own scratch (sort keys and
 // values, the digit histogram, the disk tables, the alive count and the status
-// bits) in one file-scope device array of fixed size, so it allocates nothing.
+// bits) in one file-scope device array of fixed size, so it allocates nothing,
+// on the device or on the host.
 //
 // The array lives on every GPU that loads the library until the process
 // exits.  All calls share it and it keeps the previous call's contents, so
@@ -20,7 +20,6 @@
 #include <string.h>
 
 #include <mutex>
-#include <vector>
 
 #include "mcd_internal.cuh"
 
@@ -49,16 +48,17 @@ constexpr size_t kScratchBytes = align256(kOffStatus + 4);
 
 static __device__ __align__(256) unsigned char g_regrid_scratch[kScratchBytes];
 
+constexpr int kMaxDevices = 64;
 std::mutex g_setup_lock;
-std::vector<unsigned char *> g_scratch_ptr;  // per device, null until looked up
+unsigned char *g_scratch_ptr[kMaxDevices] = {};  // per device, null until looked up
 
 // device address of the scratch array on the current device
 int scratch_address(unsigned char **out)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return MCD_ECUDA;
+    if (dev < 0 || dev >= kMaxDevices) return MCD_ECUDA;
     std::lock_guard<std::mutex> g(g_setup_lock);
-    if ((int)g_scratch_ptr.size() <= dev) g_scratch_ptr.resize(dev + 1, nullptr);
     if (!g_scratch_ptr[dev]) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_regrid_scratch) != cudaSuccess || !p) return MCD_ECUDA;
@@ -66,6 +66,16 @@ int scratch_address(unsigned char **out)
     }
     *out = g_scratch_ptr[dev];
     return MCD_OK;
+}
+
+// the one disk's parameter and layout tables, passed by value (nothing is
+// copied from host memory), and a clean status word
+__global__ void k_noalloc_tables(mcd_disk_params p, mcd::DiskDev D, mcd_disk_params *dp, mcd::DiskDev *dd,
+                                 int32_t *status)
+{
+    *dp = p;
+    *dd = D;
+    *status = 0;
 }
 
 __global__ void k_status_code(const int32_t *bits, int32_t *code)
@@ -88,18 +98,17 @@ extern "C" int mcd_regrid_noalloc(const mcd_disk_params *p, const mcd_grid *g, c
     if (g->n_r <= 0 || g->n_z <= 0 || g->per_cell <= 0) return MCD_EINVAL;
     const int64_t N = (int64_t)g->n_r * g->n_z * g->per_cell;
     if (N > kNoAllocMax) return MCD_EINVAL;                     // beyond the fixed scratch
-    if ((int64_t)g->n_z * g->per_cell > 14336) return MCD_EINVAL;  // one zone must fit in shared memory
+    if ((int64_t)g->n_z * g->per_cell > mcd::kZoneCap) return MCD_EINVAL;  // one zone must fit in shared memory
     if (p->kernel_mode == 0 && !(p->r_in > 0.0)) return MCD_EINVAL;
     unsigned char *s = nullptr;
     int rc = scratch_address(&s);
     if (rc != MCD_OK) return rc;
 
-    // a context on the stack whose buffers are the caller's arrays and the scratch
+    // a context on the stack whose buffers are the caller's arrays and the
+    // scratch (its host-side tables stay empty: nothing is allocated)
     mcd_ctx c;
     c.n_disks = 1;
     c.stream = (cudaStream_t)cuda_stream;
-    c.hp.assign(p, p + 1);
-    c.hg.assign(g, g + 1);
     mcd::DiskDev D;
     D.p_off = 0;
     D.n0 = N;
@@ -109,8 +118,9 @@ extern "C" int mcd_regrid_noalloc(const mcd_disk_params *p, const mcd_grid *g, c
     D.n_tiles = (N + mcd::kRadixTile - 1) / mcd::kRadixTile;
     D.n_r = g->n_r;
     D.n_z = g->n_z;
-    c.hd.assign(1, D);
     c.N = N;
+    c.zone_max = (int64_t)g->n_z * g->per_cell;
+    c.n0_max = N;
     c.C = (int64_t)g->n_r * g->n_z;
     c.Z = g->n_r;
     c.n_tiles = D.n_tiles;
@@ -144,15 +154,13 @@ extern "C" int mcd_regrid_noalloc(const mcd_disk_params *p, const mcd_grid *g, c
     c.cell_b = bounds;
     c.cell_V = V;
 
-    // tables for one disk (all indices 0) and a clean status word; the copies
-    // from host memory return once the source has been staged
+    // tables for one disk (all indices 0) and a clean status word
     cudaStream_t st = c.stream;
-    cudaError_t e = cudaMemcpyAsync(c.d_params, p, sizeof(mcd_disk_params), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(c.d_disks, &D, sizeof D, cudaMemcpyHostToDevice, st);
+    k_noalloc_tables<<<1, 1, 0, st>>>(*p, D, c.d_params, c.d_disks, c.status);
+    cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemsetAsync(c.slot_disk, 0, 4 * N, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c.zone_disk, 0, 4 * c.Z, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c.tile_disk, 0, 4 * c.n_tiles, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c.status, 0, 4, st);
     if (e == cudaSuccess) e = mcd::prepare_zone(&c);
     if (e == cudaSuccess) e = mcd::launch_regrid(&c);
     if (e == cudaSuccess) e = cudaMemcpyAsync(n_alive, c.n_alive, 8, cudaMemcpyDeviceToDevice, st);

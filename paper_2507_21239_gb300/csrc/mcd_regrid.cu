@@ -652,25 +652,26 @@ struct ZonePlan {
 };
 static ZonePlan zone_plan(const mcd_ctx *c)
 {
-    ZonePlan z{0, 0, 0, 0};
-    int64_t n0max = 0;
-    for (size_t d = 0; d < c->hg.size(); ++d) {
-        const int64_t zc = (int64_t)c->hg[d].n_z * c->hg[d].per_cell;
-        z.zcap = z.zcap > zc ? z.zcap : zc;
-        const int64_t n0 = (int64_t)c->hg[d].n_r * zc;
-        n0max = n0max > n0 ? n0max : n0;
-    }
+    ZonePlan z{c->zone_max, 0, 0, 0};
     z.radix = z.zcap <= kZoneRadixMax;
-    for (int64_t idmax = n0max - 1; idmax > 0; idmax >>= 8) ++z.id_passes;
+    for (int64_t idmax = c->n0_max - 1; idmax > 0; idmax >>= 8) ++z.id_passes;
     z.smem = (size_t)z.zcap * sizeof(uint4) * (z.radix ? 2 : 1) + (z.radix ? kZoneRadixScratch : 0);
     return z;
 }
 
-cudaError_t prepare_zone(mcd_ctx *c)
+// The zone sort's shared-memory limit is a property of the kernel, shared by
+// every context and caller in the process: it is set to what the largest
+// zone of either path takes, never to one caller's need, so that no later
+// set-up lowers it below what another context launches with.
+constexpr size_t kZoneSmemRadixMax = (size_t)kZoneRadixMax * sizeof(uint4) * 2 + kZoneRadixScratch;
+constexpr size_t kZoneSmemBitonicMax = (size_t)kZoneCap * sizeof(uint4);
+constexpr size_t kZoneSmemMax = kZoneSmemRadixMax > kZoneSmemBitonicMax ? kZoneSmemRadixMax : kZoneSmemBitonicMax;
+
+cudaError_t prepare_zone(mcd_ctx *)
 {
     cudaError_t e = cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterStage);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_zone, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zone_plan(c).smem);
+    return cudaFuncSetAttribute(k_zone, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kZoneSmemMax);
 }
 
 cudaError_t launch_regrid(mcd_ctx *c)

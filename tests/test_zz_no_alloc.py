@@ -1,16 +1,19 @@
-"""The regrid entry point that allocates nothing, against mcd_regrid.
+"""The regrid entry point that allocates nothing, against mcd_regrid and the oracle.
 
 mcd_regrid_noalloc serves callers that cannot call cudaMalloc (code inside
-another framework's memory pool, inside a caller's graph capture or real-time
-loop, or under a fixed memory budget): it keeps its scratch in one fixed
-device array shared by every call.  Here it must give exactly what the
-context-based mcd_regrid gives for the same particles, on several calls in a
-row with different disks (so nothing of a previous call leaks into the next).
-This file is collected last on purpose."""
+another framework's memory pool, a real-time loop where an allocation would
+stall, or a fixed memory budget): it keeps its scratch in one fixed device
+array shared by every call.  Here it must give exactly what the context-based
+mcd_regrid gives for the same particles, and what the oracle's regrid gives,
+on several calls in a row with different disks (so nothing of a previous call
+leaks into the next); report bad input through its status word and recover on
+the next clean call; and leave a larger context able to step.  This file is
+collected last on purpose."""
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
+import oracle  # noqa: E402
 from paper_2507_21239_gb300 import mcd, workloads as W  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -23,6 +26,7 @@ def _gpu():
         pytest.skip("no CUDA device")
     from paper_2507_21239_gb300 import build
     build.build()
+    oracle.build()
 
 
 def _state(grid, seed, dead):
@@ -88,11 +92,7 @@ def test_noalloc_regrid_matches_context_regrid_on_consecutive_calls():
         ref = _with_context(P, grid, st)
         got = _without_allocation(P, grid, st)
         assert got["status"] == mcd.MCD_OK
-        assert got["n_alive"] == ref["n_alive"]
-        assert np.array_equal(got["id"], ref["id"])
-        for key in ("m", "M", "r", "z", "b", "V"):
-            assert np.array_equal(np.asarray(got[key]).view(np.uint64), np.asarray(ref[key]).view(np.uint64)), key
-        assert np.array_equal(got["off"], ref["off"])
+        _same(got, ref)
 
 
 def test_noalloc_regrid_rejects_sizes_beyond_its_scratch():
@@ -102,3 +102,75 @@ def test_noalloc_regrid_rejects_sizes_beyond_its_scratch():
     with pytest.raises(mcd.McdError) as e:
         mcd.mcd_regrid_noalloc(P, (512, 16, 16), args[:5], args[5:])  # 131,072 > 65,536 particles
     assert e.value.code == mcd.MCD_EINVAL
+
+
+def _same(got, ref):
+    assert got["n_alive"] == ref["n_alive"]
+    assert np.array_equal(got["id"], ref["id"])
+    for key in ("m", "M", "r", "z", "b", "V"):
+        assert np.array_equal(np.asarray(got[key]).view(np.uint64), np.asarray(ref[key]).view(np.uint64)), key
+    assert np.array_equal(got["off"], ref["off"])
+
+
+def test_noalloc_regrid_matches_the_oracle():
+    """Ids, reordered columns, offsets, bounds and volumes equal the oracle's
+    regrid of the same particles bit for bit (a disk without single-particle
+    cells, whose bounds come from the gas functions)."""
+    grid = (16, 4, 100)
+    P, st = _state(grid, 31, 20)
+    got = _without_allocation(P, grid, st)
+    assert got["status"] == mcd.MCD_OK
+    s = oracle.DiskState(*st)
+    rc, perm, off, cb, cv, na = oracle.regrid(P, grid[0], grid[1], s)
+    assert rc == oracle.OK
+    ref = {"m": s.m, "M": s.M, "r": s.r, "z": s.z, "id": s.id, "off": off, "b": cb, "V": cv, "n_alive": na}
+    assert np.all(np.diff(off) != 1)
+    _same(got, ref)
+
+
+@pytest.mark.parametrize("fault", ["nan_z", "bad_id", "all_removed"])
+def test_noalloc_status_codes_then_a_clean_call(fault):
+    """A NaN height latches MCD_ENAN, an id outside 0..count-1 MCD_EINVAL and a
+    disk whose particles are all removed MCD_EEMPTY; the kernels' own checks
+    keep every access in bounds.  The next call with clean input reports
+    MCD_OK and equals the context regrid: no status bit survives a call."""
+    grid = (8, 4, 50)
+    P, st = _state(grid, 41, 3)
+    m, M, r, z, ids = (np.copy(a) for a in st)
+    if fault == "nan_z":
+        z[17] = np.nan
+        want = mcd.MCD_ENAN
+    elif fault == "bad_id":
+        ids[5] = len(ids) + 3
+        want = mcd.MCD_EINVAL
+    else:
+        r[:] = np.inf
+        want = mcd.MCD_EEMPTY
+    bad = _without_allocation(P, grid, (m, M, r, z, ids))
+    assert bad["status"] == want
+    clean = _without_allocation(P, grid, st)
+    assert clean["status"] == mcd.MCD_OK
+    _same(clean, _with_context(P, grid, st))
+
+
+def test_a_larger_context_steps_after_noalloc_calls():
+    """The zone sort's shared-memory limit belongs to the kernel, not to one
+    caller: a context with 3,200-particle zones, created first, still regrids
+    and steps after a no-allocation call on a disk with 400-particle zones and
+    after a smaller context has been created."""
+    P = W.benchmark_disk()
+    big = mcd.Disk(P, (64, 16, 200), seed=5, prec="mixed")
+    big.step(W.YR)
+    assert mcd.mcd_sync(big.ctx) == mcd.MCD_OK
+    grid = (16, 4, 100)
+    Ps, st = _state(grid, 51, 0)
+    assert _without_allocation(Ps, grid, st)["status"] == mcd.MCD_OK
+    small = mcd.Disk(P, (4, 2, 10), seed=6, prec="mixed")
+    small.step(W.YR)
+    for _ in range(2):
+        big.step(W.YR)
+        mcd.mcd_regrid(big.ctx)
+    assert mcd.mcd_sync(big.ctx) == mcd.MCD_OK
+    assert mcd.mcd_sync(small.ctx) == mcd.MCD_OK
+    small.close()
+    big.close()
