@@ -27,15 +27,21 @@ DV_BM, DV_TURB, DV_RAD, DV_PHI, DV_SET = 1, 2, 4, 8, 16
 TR_RADIAL, TR_VERTICAL, TR_ST_MIDPLANE = 1, 2, 4
 
 
+def compile_lib(src: str, out: str) -> str:
+    """gcc -O2, FP contraction off, OpenMP on: src -> shared library out."""
+    tmp = out + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (FP contraction off, OpenMP on)."""
+    """Compile the oracle."""
     with _lock:
         if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-            tmp = _LIB + f".{os.getpid()}.tmp"
-            cmd = ["gcc", "-O2", "-std=gnu11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
-                   "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
-            subprocess.run(cmd, check=True)
-            os.replace(tmp, _LIB)
+            compile_lib(_SRC, _LIB)
     return _LIB
 
 
@@ -88,52 +94,59 @@ def lib():
     global _lib
     if _lib is None:
         build()
-        L = C.CDLL(_LIB)
-        L.orc_philox4x64_10.argtypes = [_u64, _u64, _u64]
-        L.orc_gas_probe.argtypes = [_P(Params), C.c_int64, _d, _d, _d]
-        L.orc_particle_probe.argtypes = [_P(Params), C.c_double, C.c_double, C.c_int64, _d, _d, _d, _i32]
-        L.orc_pair_probe.argtypes = [_P(Params), C.c_double, C.c_double, C.c_int64, _d, _d, _d, _d, _d, _d]
-        L.orc_rate_matrix.argtypes = [_P(Params), C.c_double, C.c_double, C.c_double, C.c_int64, _d, _d, _d, _d]
-        L.orc_fragment_probe.argtypes = [_P(Params), C.c_double, C.c_double, C.c_double]
-        L.orc_fragment_probe.restype = C.c_double
-        L.orc_outcome_probe.argtypes = [_P(Params), C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
-                                        _P(C.c_int32)]
-        L.orc_outcome_probe.restype = C.c_double
-        L.orc_disk_dust_mass.argtypes = [_P(Params)]
-        L.orc_disk_dust_mass.restype = C.c_double
-        L.orc_collide_cell.argtypes = [_P(Params), C.c_double, C.c_double, C.c_double, C.c_int64, _d, _d,
-                                       C.c_double, C.c_double, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64,
-                                       C.c_int64, C.c_int64, _i64, _d, _P(Event), C.c_int64]
-        L.orc_init_disk.argtypes = [_P(Params), C.c_int64, C.c_uint64, C.c_uint64, _d, _d, _d, _d, _u32]
-        L.orc_regrid.argtypes = [_P(Params), C.c_int32, C.c_int32, C.c_int64, _d, _d, _d, _d, _u32, _i64, _i64,
-                                 _d, _d, _i64]
-        L.orc_transport.argtypes = [_P(Params), C.c_int64, _d, _d, _d, _d, _u32, C.c_double, C.c_uint64,
-                                    C.c_uint64, C.c_uint64, _d]
-        L.orc_collide_all.argtypes = [_P(Params), C.c_int32, C.c_int32, _i64, _d, _d, _d, _d, C.c_double,
-                                      C.c_double, C.c_uint64, C.c_uint64, C.c_uint64, C.c_int64, C.c_int64,
-                                      _i64, C.c_int32]
-        L.orc_run.argtypes = [_P(Params), C.c_int32, C.c_int32, C.c_int64, _d, _d, _d, _d, _u32, C.c_double,
-                              C.c_double, C.c_int64, C.c_int64, C.c_uint64, C.c_uint64, C.c_int64, C.c_int64,
-                              _d, _i64, C.c_int32]
-        L.orc_moments.argtypes = [C.c_int64, _d, _d, _d, C.c_int32, _d, _d]
-        L.orc_tracer_update.argtypes = [_P(Params), C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
-                                        C.c_int32]
-        L.orc_tracer_update.restype = C.c_double
-        L.orc_collide_cell_q.argtypes = [_P(Params), C.c_double, C.c_double, C.c_double, C.c_int64, _d, _d, _d,
-                                         C.c_double, C.c_double, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64,
-                                         C.c_int64, C.c_int64, _i64, _d, _P(Event), C.c_int64]
-        L.orc_run_q.argtypes = [_P(Params), C.c_int32, C.c_int32, C.c_int64, _d, _d, _d, _d, _u32, _d, C.c_double,
-                                C.c_double, C.c_int64, C.c_int64, C.c_uint64, C.c_uint64, C.c_int64, C.c_int64,
-                                _d, _i64, C.c_int32]
-        L.orc_sigma_map.argtypes = [C.c_int64, _d, _d, _d, C.c_int32, _d, C.c_int32, _d, _d]
-        L.orc_adaptive_dt.argtypes = [_P(Params), C.c_int64, _i64, _d, C.c_int64, _d, _d, _d, C.c_double,
-                                      C.c_double]
-        L.orc_adaptive_dt.restype = C.c_double
-        L.orc_run_adaptive.argtypes = [_P(Params), C.c_int32, C.c_int32, C.c_int64, _d, _d, _d, _d, _u32, _d,
-                                       C.c_double, C.c_double, C.c_double, C.c_int64, C.c_int64, C.c_uint64,
-                                       C.c_uint64, C.c_int64, C.c_int64, _d, _i64, C.c_int32, _d]
-        _lib = L
+        _lib = load(_LIB)
     return _lib
+
+
+def load(path: str):
+    """The oracle library at path with its argument types declared (the
+    tests also load copies built from altered source, to check that the pins
+    catch planted mistakes)."""
+    L = C.CDLL(path)
+    L.orc_philox4x64_10.argtypes = [_u64, _u64, _u64]
+    L.orc_gas_probe.argtypes = [_P(Params), C.c_int64, _d, _d, _d]
+    L.orc_particle_probe.argtypes = [_P(Params), C.c_double, C.c_double, C.c_int64, _d, _d, _d, _i32]
+    L.orc_pair_probe.argtypes = [_P(Params), C.c_double, C.c_double, C.c_int64, _d, _d, _d, _d, _d, _d]
+    L.orc_rate_matrix.argtypes = [_P(Params), C.c_double, C.c_double, C.c_double, C.c_int64, _d, _d, _d, _d]
+    L.orc_fragment_probe.argtypes = [_P(Params), C.c_double, C.c_double, C.c_double]
+    L.orc_fragment_probe.restype = C.c_double
+    L.orc_outcome_probe.argtypes = [_P(Params), C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                    _P(C.c_int32)]
+    L.orc_outcome_probe.restype = C.c_double
+    L.orc_disk_dust_mass.argtypes = [_P(Params)]
+    L.orc_disk_dust_mass.restype = C.c_double
+    L.orc_collide_cell.argtypes = [_P(Params), C.c_double, C.c_double, C.c_double, C.c_int64, _d, _d,
+                                   C.c_double, C.c_double, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64,
+                                   C.c_int64, C.c_int64, _i64, _d, _P(Event), C.c_int64]
+    L.orc_init_disk.argtypes = [_P(Params), C.c_int64, C.c_uint64, C.c_uint64, _d, _d, _d, _d, _u32]
+    L.orc_regrid.argtypes = [_P(Params), C.c_int32, C.c_int32, C.c_int64, _d, _d, _d, _d, _u32, _i64, _i64,
+                             _d, _d, _i64]
+    L.orc_transport.argtypes = [_P(Params), C.c_int64, _d, _d, _d, _d, _u32, C.c_double, C.c_uint64,
+                                C.c_uint64, C.c_uint64, _d]
+    L.orc_collide_all.argtypes = [_P(Params), C.c_int32, C.c_int32, _i64, _d, _d, _d, _d, C.c_double,
+                                  C.c_double, C.c_uint64, C.c_uint64, C.c_uint64, C.c_int64, C.c_int64,
+                                  _i64, C.c_int32]
+    L.orc_run.argtypes = [_P(Params), C.c_int32, C.c_int32, C.c_int64, _d, _d, _d, _d, _u32, C.c_double,
+                          C.c_double, C.c_int64, C.c_int64, C.c_uint64, C.c_uint64, C.c_int64, C.c_int64,
+                          _d, _i64, C.c_int32]
+    L.orc_moments.argtypes = [C.c_int64, _d, _d, _d, C.c_int32, _d, _d]
+    L.orc_tracer_update.argtypes = [_P(Params), C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                    C.c_int32]
+    L.orc_tracer_update.restype = C.c_double
+    L.orc_collide_cell_q.argtypes = [_P(Params), C.c_double, C.c_double, C.c_double, C.c_int64, _d, _d, _d,
+                                     C.c_double, C.c_double, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64,
+                                     C.c_int64, C.c_int64, _i64, _d, _P(Event), C.c_int64]
+    L.orc_run_q.argtypes = [_P(Params), C.c_int32, C.c_int32, C.c_int64, _d, _d, _d, _d, _u32, _d, C.c_double,
+                            C.c_double, C.c_int64, C.c_int64, C.c_uint64, C.c_uint64, C.c_int64, C.c_int64,
+                            _d, _i64, C.c_int32]
+    L.orc_sigma_map.argtypes = [C.c_int64, _d, _d, _d, C.c_int32, _d, C.c_int32, _d, _d]
+    L.orc_adaptive_dt.argtypes = [_P(Params), C.c_int64, _i64, _d, C.c_int64, _d, _d, _d, C.c_double,
+                                  C.c_double]
+    L.orc_adaptive_dt.restype = C.c_double
+    L.orc_run_adaptive.argtypes = [_P(Params), C.c_int32, C.c_int32, C.c_int64, _d, _d, _d, _d, _u32, _d,
+                                   C.c_double, C.c_double, C.c_double, C.c_int64, C.c_int64, C.c_uint64,
+                                   C.c_uint64, C.c_int64, C.c_int64, _d, _i64, C.c_int32, _d]
+    return L
 
 
 def _ptr(a, ct):

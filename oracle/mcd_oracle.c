@@ -19,9 +19,12 @@
  * with -ffp-contract=off so that no multiply-add is fused behind its back.
  *
  * Parity status: every function here is pinned by a test in tests/ against a
- * closed form, an invariant, brute force or a library routine, except the
- * absolute physical outcome of full disk runs (the paper prints no numbers for
- * them), which is "parity unpinned".
+ * closed form, an invariant, brute force, a library routine or a numerical
+ * integral (the gas state at 1 AU against textbook definitions and printed
+ * closed-form numbers; the Ormel & Cuzzi closed forms against quadratures of
+ * their eddy-class integrals), except the absolute physical outcome of full
+ * disk runs (the paper prints no numbers for them), which is "parity
+ * unpinned".
  */
 #include <math.h>
 #include <stdint.h>

@@ -990,3 +990,198 @@ def test_grouping_keeps_the_mass_growth_rate(dm):
         assert np.allclose(got, K * M / V, rtol=1e-13, atol=0), i
     if dm > 0:  # grouping does act here: some partners are below dm m_i
         assert np.any(m[None, :] < dm * m[:, None])
+
+
+# ---- the absolute gas state at 1 AU (CGS constants of the readings) --------
+# Physical constants typed here from CODATA / IAU values, not read from the
+# oracle: Boltzmann constant, proton mass, G M_sun, the astronomical unit.
+K_B, M_P, GM_SUN = 1.380649e-16, 1.67262192e-24, 1.32712440018e26
+
+
+def _check_gas_state_1au():
+    """The gas at 1 AU, midplane, of the benchmark disk (T = 280 K, Sigma_g =
+    1000 g cm^-2, mu = 2.34, sigma_H2 = 2e-15 cm^2, alpha = 1e-3): the closed-form
+    numbers c_s = 9.94e4 cm/s, Omega = 1.99e-7 s^-1, H = 4.99e11 cm, rho_mid =
+    7.99e-10 g cm^-3 and lambda = 2.45 cm, each to its printed digits, and the
+    same fields to 1e-12 from the textbook definitions evaluated here: the
+    isothermal sound speed sqrt(k_B T / (mu m_p)), the Keplerian frequency, the
+    Gaussian midplane density Sigma / (sqrt(2 pi) H), the mean free path
+    1 / (n sigma_H2) with n = rho / (mu m_p), the mean thermal speed
+    sqrt(8/pi) c_s, the molecular viscosity nu = v_th lambda / 2, the turbulent
+    diffusivity alpha c_s H, the large-eddy velocity V_g^2 = 3/2 alpha c_s^2
+    and the Kolmogorov Stokes number St_eta = Re^-1/2 with Re = alpha c_s H / nu."""
+    g = {k: v[0] for k, v in oracle.gas(P0, AU, 0.0).items()}
+    printed = {"cs": 9.94e4, "Omega": 1.99e-7, "H": 4.99e11, "rho": 7.99e-10, "lambda": 2.45}
+    for k, v in printed.items():
+        assert abs(g[k] / v - 1) < 0.6e-2, (k, g[k], v)  # three significant digits
+    mu, T, S = P0["mu"], P0["T0"], P0["sigma0"]
+    cs = np.sqrt(K_B * T / (mu * M_P))
+    Om = np.sqrt(GM_SUN / AU**3)
+    H = cs / Om
+    rho = S / (np.sqrt(2 * np.pi) * H)
+    lam = 1.0 / (rho / (mu * M_P) * P0["sigma_h2"])
+    vth = np.sqrt(8 / np.pi) * cs
+    nu = 0.5 * vth * lam
+    D = P0["alpha"] * cs * H
+    ref = {"cs": cs, "Omega": Om, "H": H, "rho": rho, "lambda": lam, "vth": vth, "nu": nu, "D": D,
+           "vg2": 1.5 * P0["alpha"] * cs**2, "St_eta": (D / nu) ** -0.5, "asw": 2.25 * lam}
+    for k, v in ref.items():
+        assert abs(g[k] / v - 1) < 1e-12, (k, g[k], v)
+
+
+def _check_monomer_stokes_number_1au():
+    """A 1 um, 1.6 g cm^-3 monomer at 1 AU in the midplane couples in the
+    Epstein regime with St = 2.5e-7 (two printed digits)."""
+    m0 = 4 / 3 * np.pi * P0["rho_s"] * P0["a_mono"] ** 3
+    a, St, stk = oracle.particle(P0, AU, 0.0, m0)
+    assert stk[0] == 0 and abs(a[0] / P0["a_mono"] - 1) < 1e-14
+    assert abs(St[0] / 2.5e-7 - 1) < 0.02, St[0]
+
+
+def test_gas_state_at_1au():
+    _check_gas_state_1au()
+
+
+def test_monomer_stokes_number_at_1au():
+    _check_monomer_stokes_number_1au()
+
+
+# ---- Ormel & Cuzzi (2007): the closed forms against their eddy integrals ----
+# In the model behind the closed forms (Volk et al. 1980; Ormel & Cuzzi 2007,
+# their section 3), a Kolmogorov cascade spans eddy turnover times t from the
+# Kolmogorov scale t_eta = Re^-1/2 to the largest eddy t = 1 (in units of
+# 1/Omega), and carries the same kinetic energy V_g^2 dt per interval dt.
+# Eddies slower than t* are "class I" (both grains' motions stay correlated
+# with the eddy); faster ones are "class II" (each grain gets an independent
+# kick).  With St_1 >= St_2 the per-eddy contributions to dv^2 / V_g^2 are
+#   class I:  (St_1 - St_2)/(St_1 + St_2) [St_1^2/(St_1 + t)^2 - St_2^2/(St_2 + t)^2]
+#   class II: sum over the two grains of 1 - St_i^2/(St_i + t)^2,
+# and the class boundary is t* = y_a St_1 (y_a = 1.6) for St_eta <= St_1 < 1,
+# t* = 1 above (every eddy class II) and t* = t_eta below (every eddy class I).
+# The closed forms are these integrals with the terms of order St_1^2 (the
+# largest eddies) and t_eta (the smallest) dropped.
+Y_A = 1.6
+
+
+def _oc07_dv2_quadrature(S1, S2, t_eta):
+    S1, S2 = max(S1, S2), min(S1, S2)
+    t_star = t_eta if S1 < t_eta else min(max(Y_A * S1, t_eta), 1.0)
+
+    def class1(t):
+        return (S1 - S2) / (S1 + S2) * (S1**2 / (S1 + t) ** 2 - S2**2 / (S2 + t) ** 2)
+
+    def class2(t):
+        return (1 - S1**2 / (S1 + t) ** 2) + (1 - S2**2 / (S2 + t) ** 2)
+
+    kw = dict(epsabs=0, epsrel=1e-12, limit=400)
+    v1 = integrate.quad(class1, t_star, 1.0, **kw)[0] if t_star < 1.0 else 0.0
+    v2 = integrate.quad(class2, t_eta, t_star, **kw)[0] if t_star > t_eta else 0.0
+    return v1 + v2
+
+
+# a gas with a 100x larger molecular cross section: Re 100x larger, St_eta
+# 10x smaller (6.3e-6 at 1 AU), so that the dropped t_eta terms are small
+P_OC = W.benchmark_disk(dv_flags=2, sigma_h2=2e-13)
+
+
+def _oc07_case(S1_target, eps):
+    r = AU
+    g = oracle.gas(P_OC, r, 0.0)
+    t_eta, vg2 = g["St_eta"][0], g["vg2"][0]
+    m1 = _mass_for_St(P_OC, r, 0.0, S1_target)
+    m2 = _mass_for_St(P_OC, r, 0.0, eps * S1_target)
+    S1 = oracle.particle(P_OC, r, 0.0, m1)[1][0]
+    S2 = oracle.particle(P_OC, r, 0.0, m2)[1][0]
+    dv = oracle.pairs(P_OC, r, 0.0, m1, m2)["dv"][0]
+    return dv**2 / vg2, _oc07_dv2_quadrature(S1, S2, t_eta), S1, S2, t_eta
+
+
+OC_EPS = (1.0, 0.3, 0.05, 1e-6)
+
+
+def _check_oc07_regime_II():
+    """Intermediate regime, St_eta << St_1 << 1: the closed form of Ormel &
+    Cuzzi against the quadrature with t* = y_a St_1.  The dropped terms are at
+    most St_1^2 (largest eddies) and 2 t_eta (smallest) against a total of at
+    least 1.97 St_1, which sets the bound."""
+    for S1t in (3e-3, 1e-2):
+        for eps in OC_EPS:
+            closed, quad, S1, S2, t_eta = _oc07_case(S1t, eps)
+            assert t_eta < S1 < 1
+            bound = (S1**2 + 2 * t_eta) / (1.97 * S1) + 1e-9
+            assert abs(closed / quad - 1) < bound, (S1, S2, closed, quad, bound)
+
+
+def _check_oc07_regime_I():
+    """Tightly coupled regime, St_1 < St_eta: every eddy is class I; the dropped
+    largest-eddy terms are of relative order t_eta / (1 - eps)^2."""
+    for eps in (0.3, 0.05, 1e-6):
+        closed, quad, S1, S2, t_eta = _oc07_case(0.3 * oracle.gas(P_OC, AU, 0.0)["St_eta"][0], eps)
+        assert S1 < t_eta
+        assert abs(closed / quad - 1) < 4 * t_eta / (1 - eps) ** 2, (S1, S2, closed, quad)
+
+
+def _check_oc07_regime_III():
+    """Heavy regime, St_1 >= 1: every eddy is class II; the dropped terms are
+    the smallest eddies' 2 t_eta against a total of at least 2 / (1 + St_1)."""
+    for S1t in (3.0, 30.0):
+        for eps in OC_EPS:
+            closed, quad, S1, S2, t_eta = _oc07_case(S1t, eps)
+            assert S1 >= 1
+            assert abs(closed / quad - 1) < t_eta * (1 + S1) + 1e-9, (S1, S2, closed, quad)
+
+
+def test_turbulence_regime_II_equals_its_eddy_integral():
+    _check_oc07_regime_II()
+
+
+def test_turbulence_regime_I_equals_its_eddy_integral():
+    _check_oc07_regime_I()
+
+
+def test_turbulence_regime_III_equals_its_eddy_integral():
+    _check_oc07_regime_III()
+
+
+# ---- planted mistakes: each altered copy of the oracle fails a pin ----------
+PLANTED = {
+    "mu_2pct": ("g.cs = sqrt(ORC_KB * g.T / (P->mu * ORC_MP));",
+                "g.cs = sqrt(ORC_KB * g.T / (1.02 * P->mu * ORC_MP));"),
+    "lambda_sqrt2": ("g.lambda = P->mu * ORC_MP / (g.rho * P->sigma_h2);",
+                     "g.lambda = P->mu * ORC_MP / (sqrt(2.0) * g.rho * P->sigma_h2);"),
+    "nu_third": ("g.nu = 0.5 * g.vth * g.lambda;", "g.nu = (1.0 / 3.0) * g.vth * g.lambda;"),
+    "vg2_1": ("g.vg2 = 1.5 * P->alpha * g.cs * g.cs;", "g.vg2 = 1.0 * P->alpha * g.cs * g.cs;"),
+    "ya_1.4": ("#define ORC_YA 1.6 ", "#define ORC_YA 1.4 "),
+    "eps_squared": ("eps * eps * eps / (ORC_YA + eps)", "eps * eps / (ORC_YA + eps)"),
+    "eps_factor": ("2.0 / (1.0 + eps) * (1.0 / (1.0 + ORC_YA)", "2.0 / (1.0 + ORC_YA) * (1.0 / (1.0 + ORC_YA)"),
+    "regime_III_index": ("return g->vg2 * (1.0 / (1.0 + S1) + 1.0 / (1.0 + S2));",
+                         "return g->vg2 * (1.0 / (1.0 + S1) + 1.0 / (1.0 + S1));"),
+    "regime_I_St_eta": ("(S1 * S2 + g->St_eta * s) / (s * (S1 + g->St_eta) * (S2 + g->St_eta))",
+                        "(S1 * S2 + g->St_eta * s) / (s * (S1 + g->St_eta) * (S1 + g->St_eta))"),
+}
+GAS_AND_TURBULENCE_PINS = (_check_gas_state_1au, _check_monomer_stokes_number_1au, _check_oc07_regime_I,
+                           _check_oc07_regime_II, _check_oc07_regime_III)
+
+
+@pytest.mark.parametrize("name", sorted(PLANTED))
+def test_planted_mistake_fails_a_pin(name, tmp_path, monkeypatch):
+    """A copy of the oracle with one plausible mistake in the gas state or the
+    turbulent relative velocity (a 2 % error in mu, a sqrt(2) in the mean free
+    path, 1/3 for 1/2 in the viscosity, V_g^2 = alpha c_s^2, y_a = 1.4, eps^2
+    for eps^3 or 1 + y_a for 1 + eps in regime II, a swapped index in regimes
+    I or III) fails at least one of the pins above."""
+    old, new = PLANTED[name]
+    with open(oracle._SRC) as f:
+        src = f.read()
+    assert src.count(old) == 1, name
+    path = tmp_path / "mutant.c"
+    path.write_text(src.replace(old, new))
+    lib = oracle.load(oracle.compile_lib(str(path), str(tmp_path / "libmutant.so")))
+    monkeypatch.setattr(oracle, "_lib", lib)
+    failed = []
+    for check in GAS_AND_TURBULENCE_PINS:
+        try:
+            check()
+        except AssertionError:
+            failed.append(check.__name__)
+    assert failed, f"no pin caught the planted mistake {name}"
