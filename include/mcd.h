@@ -115,20 +115,43 @@ typedef struct mcd_ctx mcd_ctx;
 #define MCD_OPT_LPT 7           /* 1: order cells by descending work estimate (default 1) */
 #define MCD_OPT_THREADS 8       /* threads per cell in collide; 0 = auto */
 #define MCD_OPT_EXCLUSIVE 9     /* 1: one collide CTA per SM, so long event chains share no SM (default 1) */
-#define MCD_OPT_DV_MATRIX 10    /* 1: keep each cell's dv_ij matrix, MCD_MIXED in shared memory when it fits
-                                   (cells of up to ~230 particles), MCD_FP64 in the workspace when every
-                                   cell's matrix together takes at most 4 GiB; 0: recompute row i at every
-                                   event.  Both give bit-identical results (default 1) */
+#define MCD_OPT_DV_MATRIX 10    /* where each cell's symmetric dv_ij matrix is kept (circulant half form,
+                                   each pair once): 1 MCD_MIXED in shared memory when it fits (cells of up
+                                   to ~314 particles), else in the workspace when reserved; 2 in the
+                                   workspace when reserved (MCD_FP64: every class, when all matrices
+                                   together take at most 8 GiB; MCD_MIXED: the classes whose matrix does
+                                   not fit in shared memory, within 16 GiB); 0 recompute row i at every
+                                   event; -1 (default) chosen per class by the timed trial.  All give
+                                   bit-identical results */
 #define MCD_OPT_TRACER 11       /* 1: every swarm carries the tracer column (mcd_get_tracer); 0 (default)
                                    clears it.  mcd_set_tracer switches it on. */
 #define MCD_OPT_DT_MAX 12       /* the largest step mcd_step(dt <= 0) takes [s] (default one year) */
 #define MCD_OPT_COURANT 13      /* C of the adaptive step (default 0.5) */
+#define MCD_OPT_SWARMS_PER_THREAD 14 /* collide threads own 1 or 2 swarms (MCD_MIXED only for 2); 0 (default)
+                                   chosen per class by the timed trial.  The mixed path's trajectories
+                                   depend on it at the level of FP32 rounding in the choice scans (the
+                                   FP64 path runs 1) */
+#define MCD_OPT_PERSISTENT 15   /* 1: persistent collide CTAs (resident ones only) take cells from the
+                                   largest-work-first queue by an atomic ticket; 0 (default) one CTA per
+                                   cell.  Results are identical */
+#define MCD_OPT_EXACT_TOTAL 17  /* MCD_MIXED, 1: the total rate that sets each waiting time, and the fresh row
+                                   sum of the last event's swarm, are compensated (TwoSum) sums of the
+                                   compensated row sums, formed by one extra warp per cell (MCD_OPT_THREADS
+                                   must then leave room for it); 0 (default): block sums of the row sums'
+                                   leading parts, relative error below 10 ulp, formed afresh each event */
+#define MCD_OPT_AUTOTUNE 16     /* 1 (default): before its first collide the context times the candidate
+                                   variants of each cell class (swarms per thread, dv-matrix store) on the
+                                   class's largest cells and keeps the fastest (mcd_get_collide_classes);
+                                   setting it to 1 again repeats the trial at the next collide */
 
 /*
  * Bytes of device workspace needed for n_disks disks at precision prec.
  * p[n_disks], g[n_disks] host arrays.  Returns MCD_EINVAL on a bad grid.
- * MCD_FP64 adds, when that is at most 4 GiB, cells x ld^2 doubles for the
- * stored dv matrices (ld = the largest particles-per-cell rounded up to odd).
+ * The stored dv matrices add, per cell class (disks grouped by particles per
+ * cell: up to 64, 128, 224, ~314, 512), cells x n_hi x W entries (W about
+ * n_hi / 2 + 1; n_hi the class's largest per_cell): MCD_FP64 for every class
+ * when all take at most 8 GiB, MCD_MIXED for the classes whose matrix does not
+ * fit in shared memory when those take at most 16 GiB.
  */
 int mcd_workspace_size(const mcd_disk_params *p, const mcd_grid *g, int32_t n_disks, int32_t prec, size_t *bytes);
 
@@ -229,6 +252,38 @@ int mcd_get_cells(mcd_ctx *ctx, int32_t disk, int64_t *cell_off, double *bounds,
 
 /* Per-particle row sums R_i after the last collide (needs MCD_OPT_DUMP_R). */
 int mcd_get_rates(mcd_ctx *ctx, int32_t disk, double *R, int32_t where);
+
+/*
+ * Per cell of the disk (n_r * n_z values, cell order): the total rate R_tot of
+ * the last choice scan of the last collide, the value that set the waiting
+ * time there (Zsom & Dullemond's event loop, Summary section; MCD_MIXED: the
+ * compensated FP32 sum of the compensated row sums, as a double).  Needs
+ * MCD_OPT_DUMP_R; with MCD_OPT_MAX_EVENTS 0 and MCD_OPT_CAP_STOPS 1 it is the
+ * total of the rebuilt row sums that mcd_get_rates returns.
+ */
+int mcd_get_total_rates(mcd_ctx *ctx, int32_t disk, double *Rtot, int32_t where);
+
+/*
+ * The collide's cell classes (disks grouped by particles per cell) and the
+ * variant each runs: threads per cell, swarms per thread, dv-matrix store,
+ * and the timed trial's candidates (the time per event of each, the median
+ * of three runs of kTrialEvents = 256 events on up to 8 of the class's
+ * largest cells).  Host memory; up to cap records, *count the number of
+ * classes.  This is the implementation's scheduling, not the paper's method.
+ */
+typedef struct {
+    int32_t n_lo, n_hi;          /* particles per cell of the class's disks */
+    int64_t cells;               /* cells in the class */
+    int32_t threads;             /* threads per cell */
+    int32_t swarms_per_thread;   /* 1 or 2 */
+    int32_t store;               /* dv matrix: 0 row i recomputed, 1 shared memory, 2 workspace */
+    int32_t persistent;          /* persistent CTAs take cells by atomic ticket */
+    int32_t tuned;               /* 1: chosen by the timed trial */
+    int32_t n_trials;            /* candidates timed (at most 8) */
+    int32_t trial_swarms[8], trial_store[8];
+    float trial_us_per_event[8]; /* the trial's time per event [us] */
+} mcd_collide_class;
+int mcd_get_collide_classes(mcd_ctx *ctx, mcd_collide_class *out, int32_t cap, int32_t *count);
 
 /* Per-cell event counts of the last collide, n_r*n_z entries. */
 int mcd_get_cell_events(mcd_ctx *ctx, int32_t disk, int64_t *events, int32_t where);
@@ -366,6 +421,25 @@ int mcd_regrid_noalloc(const mcd_disk_params *p, const mcd_grid *g, const double
                        const double *r, const double *z, const uint32_t *id, double *m_out, double *M_out,
                        double *r_out, double *z_out, uint32_t *id_out, int64_t *cell_start, int32_t *cell_n,
                        double *bounds, double *V, int64_t *n_alive, int32_t *status, void *cuda_stream);
+
+/*
+ * Microbenchmarks of this GPU (measurement only; the paper has no
+ * counterpart): shared-memory read bandwidth (conflict-free 16-byte loads,
+ * two 1024-thread CTAs per SM), FP32 and FP64 FMA throughput (eight
+ * independent chains per thread), each the median of three CUDA-event-timed
+ * runs on cuda_stream after a warm-up run; plus the SM count, the SM clock the
+ * device reports, the L2 size and the shared memory per SM.  These are the
+ * denominators of the collide kernel's rooflines.  Synchronous; allocates
+ * nothing.
+ */
+typedef struct {
+    double smem_gbs;      /* shared-memory read bandwidth, all SMs [GB/s] */
+    double fp32_tflops;   /* FP32 FMA throughput (2 flops per FMA) [TFLOP/s] */
+    double fp64_tflops;   /* FP64 FMA throughput [TFLOP/s] */
+    int32_t sm_count, sm_clock_mhz, l2_bytes, smem_per_sm_bytes;
+    float ms_smem, ms_fp32, ms_fp64;  /* the timed runs' medians [ms] */
+} mcd_peaks;
+int mcd_probe_peaks(mcd_peaks *out, void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -31,9 +31,11 @@ struct Sizes {
     int64_t N = 0, C = 0, Z = 0, T = 0;
     int32_t n_max = 0;
     std::vector<DiskDev> disks;
+    std::vector<CollideClass> cls;
+    std::vector<int32_t> disk_class;
 };
 
-int plan(const mcd_disk_params *p, const mcd_grid *g, int32_t nd, Sizes &S)
+int plan(const mcd_disk_params *p, const mcd_grid *g, int32_t nd, int32_t prec, Sizes &S)
 {
     if (!p || !g || nd <= 0) return MCD_EINVAL;
     S.disks.resize(nd);
@@ -70,20 +72,10 @@ int plan(const mcd_disk_params *p, const mcd_grid *g, int32_t nd, Sizes &S)
         if (G.per_cell > S.n_max) S.n_max = G.per_cell;
     }
     if (S.N >= ((int64_t)1 << 31)) return MCD_EINVAL;
-    return MCD_OK;
+    return plan_classes(g, nd, prec, S.cls, S.disk_class);
 }
 
-// FP64 stored dv matrices (ld x ld doubles per cell, ld = n_max rounded up to
-// odd) are reserved when they take at most this much
-constexpr size_t kFp64MatrixCap = (size_t)4 << 30;
-
-size_t fp64_matrix_bytes(const Sizes &S)
-{
-    const size_t ld = (size_t)(S.n_max | 1);
-    return (size_t)S.C * ld * ld * sizeof(double);
-}
-
-size_t carve(mcd_ctx *c, void *base, const Sizes &S, int32_t nd, int32_t prec)
+size_t carve(mcd_ctx *c, void *base, Sizes &S, int32_t nd, int32_t prec)
 {
     Carver cv(base);
     mcd_ctx tmp;
@@ -115,7 +107,12 @@ size_t carve(mcd_ctx *c, void *base, const Sizes &S, int32_t nd, int32_t prec)
     x->cell_events = cv.take<int64_t>(S.C);
     x->cell_cost = cv.take<uint32_t>(S.C);
     x->queue = cv.take<int32_t>(S.C);
-    x->qcount = cv.take<int32_t>(72);
+    x->queue_static = cv.take<int32_t>(S.C);
+    x->cell_class = cv.take<int32_t>(S.C);
+    x->qcount = cv.take<int32_t>(kMaxClasses * 64 + 8);
+    x->qheads = cv.take<int32_t>(kMaxClasses);
+    x->Rtot = cv.take<double>(S.C);
+    x->tune_scr = cv.take<unsigned long long>((size_t)nd + 2);
     x->n_alive = cv.take<int64_t>(nd);
     x->accreted = cv.take<double>(nd);
     x->events_total = cv.take<unsigned long long>(nd);
@@ -136,8 +133,9 @@ size_t carve(mcd_ctx *c, void *base, const Sizes &S, int32_t nd, int32_t prec)
     x->gas_knots = cv.take<GasKnot>((size_t)nd * kMaxGasKnots);
     x->gas_n = cv.take<int32_t>(nd);
     x->dt_acc = cv.take<unsigned long long>(2 * (size_t)nd + 1);
-    const size_t mb = fp64_matrix_bytes(S);
-    x->dvg = (prec == MCD_FP64 && mb <= kFp64MatrixCap) ? cv.take<double>(mb / sizeof(double)) : nullptr;
+    // the classes' stored dv matrices (where the plan reserves them)
+    for (CollideClass &k : S.cls) k.dvg = k.reserve ? cv.take<unsigned char>(class_matrix_bytes(k, prec)) : nullptr;
+    if (c) c->cls = S.cls;
     return (cv.off + 255) & ~(size_t)255;
 }
 
@@ -167,6 +165,21 @@ void drop_graphs(mcd_ctx *c)
             cudaGraphExecDestroy(c->gexec[k]);
             c->gexec[k] = nullptr;
         }
+}
+
+// the context's streams, events and graphs, then the context
+void destroy(mcd_ctx *c)
+{
+    drop_graphs(c);
+    for (int k = 0; k < 5; ++k)
+        if (c->tev[k]) cudaEventDestroy(c->tev[k]);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->cls_fork) cudaEventDestroy(c->cls_fork);
+    for (int q = 0; q < kMaxClasses; ++q) {
+        if (c->cls_stream[q]) cudaStreamDestroy(c->cls_stream[q]);
+        if (c->cls_join[q]) cudaEventDestroy(c->cls_join[q]);
+    }
+    delete c;
 }
 
 cudaError_t enqueue_regrid(mcd_ctx *c)
@@ -205,7 +218,7 @@ int mcd_workspace_size(const mcd_disk_params *p, const mcd_grid *g, int32_t n_di
 {
     if (!bytes || (prec != MCD_FP64 && prec != MCD_MIXED)) return MCD_EINVAL;
     Sizes S;
-    int rc = plan(p, g, n_disks, S);
+    int rc = plan(p, g, n_disks, prec, S);
     if (rc) return rc;
     *bytes = carve(nullptr, nullptr, S, n_disks, prec);
     return MCD_OK;
@@ -218,7 +231,7 @@ int mcd_init_disk(mcd_ctx **out, const mcd_disk_params *p, const mcd_grid *g, in
     if (((uintptr_t)ws & 255) != 0) return MCD_EINVAL;
     *out = nullptr;
     Sizes S;
-    int rc = plan(p, g, n_disks, S);
+    int rc = plan(p, g, n_disks, prec, S);
     if (rc) return rc;
     size_t need = carve(nullptr, nullptr, S, n_disks, prec);
     if (ws_bytes < need) return MCD_ENOMEM;
@@ -258,11 +271,30 @@ int mcd_init_disk(mcd_ctx **out, const mcd_disk_params *p, const mcd_grid *g, in
         for (int64_t k = 0; k < D.n0; ++k) slot_disk[D.p_off + k] = d;
         Msw[d] = disk_dust_mass(p[d]) / (double)D.n0;
     }
+    // collide classes: each cell's class, and the class-major cell order
+    c->cell_class_host.assign(S.C, 0);
+    for (int d = 0; d < n_disks; ++d) {
+        const DiskDev &D = S.disks[d];
+        for (int64_t k = 0; k < (int64_t)D.n_r * D.n_z; ++k) c->cell_class_host[D.c_off + k] = S.disk_class[d];
+    }
+    std::vector<int32_t> qstatic(S.C);
+    std::vector<int64_t> fill(c->cls.size(), 0);
+    for (int64_t x = 0; x < S.C; ++x) {
+        const int q = c->cell_class_host[x];
+        qstatic[c->cls[q].qoff + fill[q]++] = (int32_t)x;
+    }
     cudaStream_t st = c->stream;
     cudaError_t e = cudaSuccess;
+    if (c->cls.size() > 1) e = cudaEventCreateWithFlags(&c->cls_fork, cudaEventDisableTiming);
+    for (size_t q = 1; q < c->cls.size() && e == cudaSuccess; ++q) {
+        e = cudaStreamCreateWithFlags(&c->cls_stream[q], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->cls_join[q], cudaEventDisableTiming);
+    }
     auto cp = [&](void *dst, const void *src, size_t n) {
         if (e == cudaSuccess && n) e = cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, st);
     };
+    cp(c->cell_class, c->cell_class_host.data(), 4 * S.C);
+    cp(c->queue_static, qstatic.data(), 4 * S.C);
     cp(c->d_params, p, sizeof(mcd_disk_params) * n_disks);
     cp(c->d_disks, S.disks.data(), sizeof(DiskDev) * n_disks);
     cp(c->cell_disk, cell_disk.data(), 4 * S.C);
@@ -288,7 +320,7 @@ int mcd_init_disk(mcd_ctx **out, const mcd_disk_params *p, const mcd_grid *g, in
     if (e == cudaSuccess) e = enqueue_regrid(c);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
-        delete c;
+        destroy(c);
         return MCD_ECUDA;
     }
     c->cells_valid = true;
@@ -317,8 +349,8 @@ int mcd_collide(mcd_ctx *c, double t_end)
     }
     if (!(t_end >= c->t_host)) return MCD_EINVAL;
     if (!c->cells_valid) return MCD_ESTATE;
-    cudaError_t e = cudaSuccess;
-    if (c->lpt) e = launch_lpt(c);
+    cudaError_t e = tune_collide(c);
+    if (e == cudaSuccess && c->lpt) e = launch_lpt(c);
     if (e == cudaSuccess) e = launch_collide_impl(c, 0, t_end);
     if (e == cudaSuccess) e = launch_set_clock(c, t_end, 1, 0.0, 0);
     if (e == cudaSuccess) c->t_host = t_end;
@@ -346,7 +378,8 @@ int mcd_step(mcd_ctx *c, double dt)
         drop_graphs(c);
         c->graph_adaptive = adaptive;
     }
-    cudaError_t e = adaptive ? cudaSuccess : launch_set_clock(c, 0.0, 0, dt, 1);
+    cudaError_t e = tune_collide(c);  // (the first collide's timed trial, before any capture)
+    if (e == cudaSuccess && !adaptive) e = launch_set_clock(c, 0.0, 0, dt, 1);
     if (e != cudaSuccess) return MCD_ECUDA;
     if (c->use_graph) {
         int p = c->cur;
@@ -644,6 +677,41 @@ int mcd_get_rates(mcd_ctx *c, int32_t disk, double *R, int32_t where)
     return cuda_code(e);
 }
 
+int mcd_get_total_rates(mcd_ctx *c, int32_t disk, double *Rtot, int32_t where)
+{
+    if (!c || !Rtot || disk < 0 || disk >= c->n_disks || (where != MCD_HOST && where != MCD_DEVICE))
+        return MCD_EINVAL;
+    const DiskDev &D = c->hd[disk];
+    cudaError_t e = cudaMemcpyAsync(Rtot, c->Rtot + D.c_off, 8 * (size_t)D.n_r * D.n_z,
+                                    where == MCD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess && where == MCD_HOST) e = cudaStreamSynchronize(c->stream);
+    return cuda_code(e);
+}
+
+int mcd_get_collide_classes(mcd_ctx *c, mcd_collide_class *out, int32_t cap, int32_t *count)
+{
+    if (!c || !count || (cap > 0 && !out)) return MCD_EINVAL;
+    *count = (int32_t)c->cls.size();
+    for (int32_t q = 0; q < cap && q < (int32_t)c->cls.size(); ++q) {
+        const CollideClass &k = c->cls[q];
+        mcd_collide_class &o = out[q];
+        memset(&o, 0, sizeof o);
+        o.n_lo = k.n_lo;
+        o.n_hi = k.n_hi;
+        o.cells = k.cells;
+        collide_shape(c, q, &o.swarms_per_thread, &o.store, &o.threads);
+        o.persistent = c->persistent;
+        o.tuned = k.tuned;
+        o.n_trials = k.n_trials;
+        for (int t = 0; t < k.n_trials && t < 8; ++t) {
+            o.trial_swarms[t] = k.trial_S[t];
+            o.trial_store[t] = k.trial_store[t];
+            o.trial_us_per_event[t] = k.trial_us[t];
+        }
+    }
+    return MCD_OK;
+}
+
 int mcd_get_cell_events(mcd_ctx *c, int32_t disk, int64_t *events, int32_t where)
 {
     if (!c || disk < 0 || disk >= c->n_disks || !events || (where != MCD_HOST && where != MCD_DEVICE))
@@ -723,7 +791,20 @@ int mcd_set_option(mcd_ctx *c, int32_t key, double v)
         }
         c->tracer = v != 0.0;
         break;
-    case MCD_OPT_DV_MATRIX: c->dv_matrix = v != 0.0; break;
+    case MCD_OPT_DV_MATRIX:
+        if (!(v == -1.0 || v == 0.0 || v == 1.0 || v == 2.0)) return MCD_EINVAL;
+        c->dv_matrix = (int32_t)v;
+        break;
+    case MCD_OPT_SWARMS_PER_THREAD:
+        if (!(v == 0.0 || v == 1.0 || (v == 2.0 && c->prec == MCD_MIXED))) return MCD_EINVAL;
+        c->spt = (int32_t)v;
+        break;
+    case MCD_OPT_PERSISTENT: c->persistent = v != 0.0; break;
+    case MCD_OPT_EXACT_TOTAL: c->exact_total = v != 0.0; break;
+    case MCD_OPT_AUTOTUNE:
+        c->autotune = v != 0.0;
+        if (c->autotune) c->tuned = false;  // the next collide runs the trial again
+        break;
     case MCD_OPT_DT_MAX:
         if (!(v > 0.0) || !isfinite(v)) return MCD_EINVAL;
         c->dt_max = v;
@@ -732,7 +813,7 @@ int mcd_set_option(mcd_ctx *c, int32_t key, double v)
         if (!(v > 0.0) || !isfinite(v)) return MCD_EINVAL;
         c->courant = v;
         break;
-    case MCD_OPT_THREADS:
+    case MCD_OPT_THREADS:  // (MCD_MIXED with MCD_OPT_EXACT_TOTAL adds one helper warp to these)
         if (v != 0.0 && (v < c->n_max || v > kMaxCell || ((int)v % 32) != 0)) return MCD_EINVAL;
         c->threads = (int32_t)v;
         break;
@@ -783,11 +864,7 @@ int mcd_free(mcd_ctx *c)
 {
     if (!c) return MCD_EINVAL;
     cudaStreamSynchronize(c->stream);
-    drop_graphs(c);
-    for (int k = 0; k < 5; ++k)
-        if (c->tev[k]) cudaEventDestroy(c->tev[k]);
-    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-    delete c;
+    destroy(c);
     return MCD_OK;
 }
 

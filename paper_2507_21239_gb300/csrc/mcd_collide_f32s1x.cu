@@ -1,0 +1,21 @@
+// mcd_collide_f32s1x.cu -- the mixed-precision collide variants with 1 swarm per thread with the compensated total rate (one helper warp)
+// (every dv-matrix store, with and without the fragmentation ramp and the
+// tracer), in a translation unit of their own so that the build compiles the
+// variants in parallel.
+#include "mcd_collide.cuh"
+
+namespace mcd {
+
+template <>
+cudaError_t collide_variant<float, 1, true>(int op, int store, bool ramp, bool tracer, unsigned grid, int nthr,
+                                        size_t smem, cudaStream_t st, const CollideArgs *A, int *out)
+{
+    switch (store) {
+    case 0: return collide_variant_store<float, 1, 0, true>(op, ramp, tracer, grid, nthr, smem, st, A, out);
+    case 1: return collide_variant_store<float, 1, 1, true>(op, ramp, tracer, grid, nthr, smem, st, A, out);
+    case 2: return collide_variant_store<float, 1, 2, true>(op, ramp, tracer, grid, nthr, smem, st, A, out);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace mcd

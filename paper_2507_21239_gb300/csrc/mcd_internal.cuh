@@ -220,6 +220,34 @@ constexpr int64_t kZoneCap = 14336;
 // bytes reserved per cell for its gas/drag constants
 constexpr int kCellKBytes = 384;
 
+// Collide runs the cells in classes by particles per cell (each disk's
+// per_cell picks its class); every class has its own thread count, swarms per
+// thread and dv-matrix store, and its own launch on its own stream, so that
+// heavy chains of different classes run side by side.
+constexpr int kMaxClasses = 5;
+constexpr int kMaxTrials = 8;
+struct CollideClass {
+    int32_t n_lo = 0, n_hi = 0;  // particles per cell of the class's disks
+    int64_t cells = 0, qoff = 0; // its cells and their first queue position (class-major queue)
+    int32_t rows = 0, W = 0;     // stored matrix: rows (= n_hi) x W entries per cell (circulant half form)
+    int32_t smem_fits = 0;       // FP32: the shared-memory matrix fits one CTA
+    int32_t reserve = 0;         // the plan reserves the class's matrices in the workspace
+    void *dvg = nullptr;         // those matrices (null: not reserved)
+    int32_t S = 1, store = 0;    // swarms per thread; 0 recompute row i, 1 shared matrix, 2 workspace matrix
+    int32_t tuned = 0, n_trials = 0;
+    float trial_us[kMaxTrials] = {};  // per candidate: trial time per event on the class's largest cells
+    int32_t trial_S[kMaxTrials] = {}, trial_store[kMaxTrials] = {};
+};
+
+// row width of a circulant half matrix for cells of up to n swarms: at least
+// n/2 + 1, and 2 mod 4 (even for conflict-free reads, W/2 odd for the build)
+inline int32_t sym_width(int32_t n)
+{
+    int32_t w = n / 2 + 1;
+    while (w % 4 != 2) ++w;
+    return w;
+}
+
 }  // namespace mcd
 
 // ---- host context ------------------------------------------------------------
@@ -255,7 +283,16 @@ struct mcd_ctx {
     double *cell_b = nullptr;  // 6 per cell: r_lo r_hi z_lo z_hi r_c z_c
     double *cell_V = nullptr;
     unsigned char *cellk = nullptr;  // per-cell constants, kCellKBytes each
-    double *dvg = nullptr;           // FP64 path: stored dv matrices, ld x ld per cell (null: recompute)
+    std::vector<mcd::CollideClass> cls;  // collide classes (mcd_init_disk)
+    std::vector<int32_t> cell_class_host;  // class of each cell
+    int32_t *cell_class = nullptr;         // the same on the device [C]
+    int32_t *queue_static = nullptr;       // class-major cell order without the work estimate [C]
+    int32_t *qheads = nullptr;             // persistent CTAs: one ticket counter per class
+    double *Rtot = nullptr;                // per cell: the total rate of the last scan (MCD_OPT_DUMP_R)
+    unsigned long long *tune_scr = nullptr;  // the trial's events and status words
+    cudaStream_t cls_stream[mcd::kMaxClasses] = {};  // classes after the first run on these
+    cudaEvent_t cls_fork = nullptr, cls_join[mcd::kMaxClasses] = {};
+    int32_t n_sm = 0;
 
     int64_t *cell_events = nullptr;
     uint32_t *cell_cost = nullptr;
@@ -283,8 +320,14 @@ struct mcd_ctx {
     int64_t max_events = 10000000;  // per cell per collide call; bounds every event loop
     int32_t cap_stops = 0;
     int64_t rebuild_every = 0;
-    int32_t use_graph = 1, dump_R = 0, lpt = 1, threads = 0, exclusive = 1, dv_matrix = 1;
-    int32_t smem_optin = 0;  // dynamic shared memory the stored-dv collide variant may request
+    int32_t use_graph = 1, dump_R = 0, lpt = 1, threads = 0, exclusive = 1;
+    int32_t dv_matrix = -1;  // -1 chosen by the trial; 0 recompute; 1 stored (shared, else workspace); 2 workspace
+    int32_t spt = 0;         // swarms per thread: 0 chosen by the trial, 1 or 2
+    int32_t persistent = 0;  // 1: persistent collide CTAs take cells by atomic ticket
+    int32_t autotune = 1;    // 1: the first collide times the candidate variants of each class
+    int32_t exact_total = 0; // MCD_MIXED: the compensated total rate (one helper warp per cell)
+    bool tuned = false;
+    int32_t smem_optin = 0;  // dynamic shared memory a collide CTA may request (the device's opt-in limit)
     int32_t ramp = 0;        // some disk has a fragmentation ramp (frag_ramp > 0)
     int32_t tracer = 0;      // the swarms carry the tracer column (MCD_OPT_TRACER / mcd_set_tracer)
     int32_t gas_tables = 0;  // disks with a gas table (mcd_set_gas_table)
@@ -318,6 +361,11 @@ cudaError_t launch_advance_clock(mcd_ctx *c, int add_dt_to_t);
 cudaError_t launch_adaptive_dt(mcd_ctx *c);  // writes dt into the device state
 std::vector<unsigned long long> adaptive_dt_rest(int32_t n_disks);
 cudaError_t prepare_collide(mcd_ctx *c);
+cudaError_t tune_collide(mcd_ctx *c);  // the timed trial (once per context, before the first collide)
+void collide_shape(const mcd_ctx *c, int q, int32_t *S, int32_t *store, int32_t *threads);  // class q's launch
+int plan_classes(const mcd_grid *g, int32_t nd, int32_t prec, std::vector<CollideClass> &cls,
+                 std::vector<int32_t> &disk_class);
+size_t class_matrix_bytes(const CollideClass &k, int32_t prec);  // 0: no workspace matrix for the class
 cudaError_t prepare_zone(mcd_ctx *c);
 cudaError_t launch_moments(mcd_ctx *c, int disk, int nbins);
 cudaError_t launch_sigma_map(mcd_ctx *c, int disk, int nr, int nm);

@@ -19,7 +19,8 @@ MCD_FP64, MCD_MIXED = 0, 1
 MCD_HOST, MCD_DEVICE = 0, 1
 (MCD_OPT_MAX_EVENTS, MCD_OPT_CAP_STOPS, MCD_OPT_REBUILD_EVERY, MCD_OPT_USE_GRAPH, MCD_OPT_DUMP_R,
  MCD_OPT_LOG_CELL, MCD_OPT_LPT, MCD_OPT_THREADS, MCD_OPT_EXCLUSIVE, MCD_OPT_DV_MATRIX, MCD_OPT_TRACER,
- MCD_OPT_DT_MAX, MCD_OPT_COURANT) = range(1, 14)
+ MCD_OPT_DT_MAX, MCD_OPT_COURANT, MCD_OPT_SWARMS_PER_THREAD, MCD_OPT_PERSISTENT, MCD_OPT_AUTOTUNE,
+ MCD_OPT_EXACT_TOTAL) = range(1, 18)
 PREC = {"fp64": MCD_FP64, "mixed": MCD_MIXED}
 
 
@@ -55,6 +56,20 @@ class mcd_stats(C.Structure):
                 ("accreted_mass", C.c_double), ("status", C.c_int32), ("reserved", C.c_int32)]
 
 
+class mcd_collide_class(C.Structure):
+    _fields_ = [("n_lo", C.c_int32), ("n_hi", C.c_int32), ("cells", C.c_int64), ("threads", C.c_int32),
+                ("swarms_per_thread", C.c_int32), ("store", C.c_int32), ("persistent", C.c_int32),
+                ("tuned", C.c_int32), ("n_trials", C.c_int32), ("trial_swarms", C.c_int32 * 8),
+                ("trial_store", C.c_int32 * 8), ("trial_us_per_event", C.c_float * 8)]
+
+
+class mcd_peaks(C.Structure):
+    _fields_ = [("smem_gbs", C.c_double), ("fp32_tflops", C.c_double), ("fp64_tflops", C.c_double),
+                ("sm_count", C.c_int32), ("sm_clock_mhz", C.c_int32), ("l2_bytes", C.c_int32),
+                ("smem_per_sm_bytes", C.c_int32), ("ms_smem", C.c_float), ("ms_fp32", C.c_float),
+                ("ms_fp64", C.c_float)]
+
+
 _lib = None
 _vp = C.c_void_p
 _P = C.POINTER
@@ -78,6 +93,9 @@ def lib():
         L.mcd_set_particles.argtypes = [_vp, C.c_int32, _vp, _vp, _vp, _vp, _vp, C.c_int64, C.c_int32]
         L.mcd_get_cells.argtypes = [_vp, C.c_int32, _vp, _vp, _vp, C.c_int32]
         L.mcd_get_rates.argtypes = [_vp, C.c_int32, _vp, C.c_int32]
+        L.mcd_get_total_rates.argtypes = [_vp, C.c_int32, _vp, C.c_int32]
+        L.mcd_probe_peaks.argtypes = [_P(mcd_peaks), _vp]
+        L.mcd_get_collide_classes.argtypes = [_vp, _P(mcd_collide_class), C.c_int32, _P(C.c_int32)]
         L.mcd_get_cell_events.argtypes = [_vp, C.c_int32, _vp, C.c_int32]
         L.mcd_get_event_log.argtypes = [_vp, _vp, _vp, _vp, C.c_int64, _P(C.c_int64)]
         L.mcd_get_stats.argtypes = [_vp, C.c_int32, _P(mcd_stats)]
@@ -190,6 +208,33 @@ def mcd_get_cells(ctx: int, disk: int, cell_off, bounds, V):
 
 def mcd_get_rates(ctx: int, disk: int, R, where: int = MCD_HOST):
     _check(lib().mcd_get_rates(ctx, disk, _ptr(R), where), "mcd_get_rates")
+
+
+def mcd_get_total_rates(ctx: int, disk: int, Rtot, where: int = MCD_HOST):
+    _check(lib().mcd_get_total_rates(ctx, disk, _ptr(Rtot), where), "mcd_get_total_rates")
+
+
+def mcd_probe_peaks(stream=None) -> dict:
+    """This GPU's shared-memory bandwidth and FP32/FP64 FMA throughput."""
+    out = mcd_peaks()
+    _check(lib().mcd_probe_peaks(C.byref(out), _stream_ptr(stream)), "mcd_probe_peaks")
+    return {name: getattr(out, name) for name, _ in mcd_peaks._fields_}
+
+
+def mcd_get_collide_classes(ctx: int) -> list[dict]:
+    """The collide's cell classes and the variant each runs (host records)."""
+    n = C.c_int32(0)
+    _check(lib().mcd_get_collide_classes(ctx, None, 0, C.byref(n)), "mcd_get_collide_classes")
+    buf = (mcd_collide_class * max(n.value, 1))()
+    _check(lib().mcd_get_collide_classes(ctx, buf, n.value, C.byref(n)), "mcd_get_collide_classes")
+    out = []
+    for k in buf[:n.value]:
+        t = k.n_trials
+        out.append({"n_lo": k.n_lo, "n_hi": k.n_hi, "cells": k.cells, "threads": k.threads,
+                    "swarms_per_thread": k.swarms_per_thread, "store": k.store, "persistent": k.persistent,
+                    "tuned": k.tuned, "trials": [{"swarms_per_thread": k.trial_swarms[q], "store": k.trial_store[q],
+                                                  "us_per_event": k.trial_us_per_event[q]} for q in range(t)]})
+    return out
 
 
 def mcd_get_cell_events(ctx: int, disk: int, events, where: int = MCD_HOST):

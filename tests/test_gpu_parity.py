@@ -490,14 +490,20 @@ def test_graph_replay_equals_direct_launches(prec):
     b.close()
 
 
-@pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("grid,reb", [((8, 4, 30), 0), ((4, 2, 57), 7), ((1, 1, 200), 0), ((2, 2, 224), 13)])
-def test_dv_matrix_equals_recompute(grid, reb, prec):
-    """Collide with each cell's dv matrix kept (mixed: in shared memory; FP64:
+DV_CASES = [(mcd.MCD_FP64, 1), (mcd.MCD_MIXED, 1), (mcd.MCD_MIXED, 2)]
+
+
+@pytest.mark.parametrize("prec,spt", DV_CASES, ids=["fp64", "mixed_s1", "mixed_s2"])
+@pytest.mark.parametrize("grid,reb", [((8, 4, 30), 0), ((4, 2, 57), 7), ((1, 1, 200), 0), ((2, 2, 224), 13),
+                                      ((1, 2, 312), 0), ((2, 1, 400), 11)])
+def test_dv_matrix_equals_recompute(grid, reb, prec, spt):
+    """Collide with each cell's symmetric dv matrix kept (circulant half form:
+    mixed in shared memory up to ~314 swarms and in the workspace above, FP64
     in the workspace) reaches the same bits as the path that recomputes row i
-    at every event.  Mid-run state, so sticking, erosion and fragmentation all
-    occur; reb > 0 also runs the full rebuilds from stored entries; 224
-    particles per cell is the largest matrix that fits in shared memory."""
+    at every event, for one and two swarms per thread.  Mid-run state, so
+    sticking, erosion and fragmentation all occur; reb > 0 also runs the full
+    rebuilds from stored entries; 312 swarms is a class whose matrix just fits
+    in shared memory, 400 one that takes the workspace matrix."""
     P = W.benchmark_disk()
     N = grid[0] * grid[1] * grid[2]
     m, r, z = W.midrun_state(P, N, seed=3)
@@ -505,24 +511,30 @@ def test_dv_matrix_equals_recompute(grid, reb, prec):
     r2 = P["r_in"] + (r - P["r_in"]) * (5.0 * AU / (P["r_out"] - P["r_in"]))
     r, z = r2, z * (r2 / r) ** 1.25
     out = []
-    for mat in (1, 0):
+    for mat in (1, 2, 0):
         d = _make_ctx(P, grid, seed=4, prec=prec)
         p = d.particles()
         mcd.mcd_set_particles(d.ctx, 0, m, p["M"], r, z, p["id"])
-        for key, v in ((mcd.MCD_OPT_DV_MATRIX, mat), (mcd.MCD_OPT_REBUILD_EVERY, reb), (mcd.MCD_OPT_DUMP_R, 1)):
+        for key, v in ((mcd.MCD_OPT_DV_MATRIX, mat), (mcd.MCD_OPT_REBUILD_EVERY, reb), (mcd.MCD_OPT_DUMP_R, 1),
+                       (mcd.MCD_OPT_SWARMS_PER_THREAD, spt)):
             mcd.mcd_set_option(d.ctx, key, v)
-        for _ in range(3):
+        for _ in range(2):
             d.step(YR)
         assert mcd.mcd_sync(d.ctx) == mcd.MCD_OK
+        store = mcd.mcd_get_collide_classes(d.ctx)[0]["store"]
         R = np.zeros(N)
         mcd.mcd_get_rates(d.ctx, 0, R)
-        out.append((d.particles(), d.stats().events, R))
+        out.append((d.particles(), d.stats().events, R, store))
         d.close()
-    (x, ea, Ra), (y, eb, Rb) = out
-    assert ea == eb and ea > 50
+    (x, ea, Ra, sa), (y, eb, Rb, sb), (w, ec, Rc, sc) = out
+    assert sc == 0 and sa in (1, 2) and sb in (0, 2)  # the stored paths ran where a matrix exists
+    if prec == mcd.MCD_FP64 or grid[2] > 314:
+        assert sa == 2 and sb == 2
+    assert ea == eb == ec and ea > 50
     for key in ("m", "r", "z", "id"):
-        assert np.array_equal(x[key], y[key]), key
-    assert np.array_equal(Ra, Rb)
+        assert np.array_equal(x[key], w[key]), key
+        assert np.array_equal(y[key], w[key]), key
+    assert np.array_equal(Ra, Rc) and np.array_equal(Rb, Rc)
 
 
 @pytest.mark.parametrize("prec", PRECS)
