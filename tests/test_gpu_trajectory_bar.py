@@ -1,0 +1,153 @@
+"""Statistical parity of the mixed-precision path with the oracle at the full
+bar: 32 seeds of the 16 x 4 x 100 Benchmark-table disk through 1e4 yr, and 8
+seeds of the 819,200-particle disk through its first 20 yr.
+
+The oracle's side was run once by tests/golden/make_trajectory_golden.py,
+which calls only the oracle and the seeded workload recipes, and is read here
+from its JSON fixtures: per disk the per-bin sums (M, M m, M m^2, M m^3,
+count) over 16 logarithmic radial bins and the per-bin histogram of log10 m
+(0.2 dex), the accreted and initial swarm mass.  The GPU runs the same disks
+(same seed and disk index, hence the same initial draw) in one batched
+context.
+
+Per bin that holds particles in every run of both sides:
+* the across-seed means of the bin mass and of the mass-weighted moments
+  k = 1..3 of the representative mass agree within max(2 %, 3 sigma), sigma
+  the standard error of the difference of the two means;
+* a two-sample Kolmogorov-Smirnov test of log10 m pooled over the seeds: the
+  statistic D between the two pooled distributions (on the 0.2-dex grid), its
+  p-value from the seeds' permutations (the 64 runs dealt into two groups of
+  32, 4000 times), because the particles of one run evolve together and are
+  not independent draws -- the asymptotic KS p-value, which assumes they are,
+  is reported beside it; p > 0.01 / (bins tested) (Bonferroni);
+* every disk conserves its swarm mass (alive plus accreted) to 1e-12.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+
+torch = pytest.importorskip("torch")
+from paper_2507_21239_gb300 import mcd, workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_21239_gb300 import build
+    build.build()
+
+
+def _load(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def _gpu_runs(G):
+    c = G["case"]
+    wl = W.WORKLOADS[c["workload"]]
+    P, grid = wl["params"], (wl["n_r"], wl["n_z"], wl["per_cell"])
+    edges = np.asarray(G["edges"])
+    nd = c["disks"]
+    d = mcd.Disk([P] * nd, [grid] * nd, seed=c["seed"], prec="mixed")
+    M0 = [d.particles(k)["M"].sum() for k in range(nd)]
+    for _ in range(c["steps"]):
+        d.step(c["dt_yr"] * W.YR)
+    assert mcd.mcd_sync(d.ctx) == mcd.MCD_OK
+    runs = []
+    for k in range(nd):
+        x = d.particles(k)
+        runs.append(dict(sums=d.moments(edges, k), accreted=d.stats(k).accreted_mass, M0=M0[k], m=x["m"], r=x["r"],
+                         M=x["M"]))
+    d.close()
+    return edges, runs
+
+
+def _table(sums):
+    S = np.asarray(sums)  # disks x bins x 5
+    mass = S[:, :, 0]
+    with np.errstate(invalid="ignore", divide="ignore"):
+        mk = S[:, :, 1:4] / mass[:, :, None]
+    return mass, mk, S[:, :, 4]
+
+
+def _hist(m, r, edges, hedges):
+    ok = np.isfinite(r) & (r >= edges[0]) & (r < edges[-1])
+    b = np.searchsorted(edges, r[ok], side="right") - 1
+    lm = np.clip(np.log10(m[ok]), hedges[0], np.nextafter(hedges[-1], -np.inf))
+    return [np.histogram(lm[b == q], bins=hedges)[0] for q in range(edges.size - 1)]
+
+
+def _ks_d(c1, c2):
+    """Kolmogorov-Smirnov distance of two samples given as counts on one grid."""
+    return float(np.max(np.abs(np.cumsum(c1) / c1.sum() - np.cumsum(c2) / c2.sum())))
+
+
+def _split(Hb, order, k):
+    return Hb[order[:k]].sum(0), Hb[order[k:]].sum(0)
+
+
+def _check(G, runs, edges, min_bins):
+    for x in runs:
+        alive = np.isfinite(x["r"])
+        assert abs(x["M"][alive].sum() + x["accreted"] - x["M0"]) <= 1e-12 * x["M0"]
+    for x in G["disks"]:
+        assert abs(np.asarray(x["sums"])[:, 0].sum() + x["accreted"] - x["M0"]) <= 1e-12 * x["M0"]
+    mg, kg, ng = _table([x["sums"] for x in runs])
+    mo, ko, no = _table([x["sums"] for x in G["disks"]])
+    nb = edges.size - 1
+    checked, worst = 0, []
+    for b in range(nb):
+        if not (np.all(ng[:, b] > 0) and np.all(no[:, b] > 0)):
+            continue
+        cols = [(mg[:, b], mo[:, b])] + [(kg[:, b, q], ko[:, b, q]) for q in range(3)]
+        for q, (a, o) in enumerate(cols):
+            diff = abs(a.mean() - o.mean())
+            sig = np.sqrt(a.var(ddof=1) / a.size + o.var(ddof=1) / o.size)
+            bound = max(0.02 * abs(o.mean()), 3.0 * sig)
+            worst.append((diff / bound, b, q))
+            assert diff <= bound, (b, q, a.mean(), o.mean(), sig)
+            checked += 1
+    assert checked >= 4 * min_bins
+    # KS of pooled log10 m, its p-value from permutations of whole runs
+    hedges = np.asarray(G["hist_edges"])
+    hg = np.array([_hist(x["m"], x["r"], edges, hedges) for x in runs])  # runs x bins x grid
+    ho = np.array([x["hist"] for x in G["disks"]])
+    rng = np.random.default_rng(2507)
+    H = np.concatenate([hg, ho])  # all runs
+    ng_runs = hg.shape[0]
+    pvals = []
+    for b in range(nb):
+        Hb = H[:, b, :].astype(np.float64)
+        if Hb[:ng_runs].sum() < 50 or Hb[ng_runs:].sum() < 50:
+            continue
+        D = _ks_d(Hb[:ng_runs].sum(0), Hb[ng_runs:].sum(0))
+        perm = np.array([_ks_d(*_split(Hb, rng.permutation(H.shape[0]), ng_runs)) for _ in range(4000)])
+        p = (1 + np.sum(perm >= D - 1e-12)) / (1 + perm.size)
+        n1, n2 = Hb[:ng_runs].sum(), Hb[ng_runs:].sum()
+        p_asym = float(stats.kstwobign.sf(np.sqrt(n1 * n2 / (n1 + n2)) * D))
+        pvals.append((b, float(p), float(D), p_asym))
+    assert len(pvals) >= min_bins
+    print(json.dumps({"case": G["case"], "moment_diff_over_bound_max": max(w[0] for w in worst),
+                      "ks": [{"bin": b, "p_perm": p, "D": D, "p_asymptotic": pa} for b, p, D, pa in pvals]}))
+    for b, p, D, pa in pvals:
+        assert p > 0.01 / len(pvals), (b, p, D, [(x[0], round(x[1], 4), round(x[3], 6)) for x in pvals])
+    return worst, pvals
+
+
+def test_32_seeds_through_1e4_yr_match_the_oracle_in_distribution():
+    G = _load("trajectory_16x4x100_1e4yr.json")
+    edges, runs = _gpu_runs(G)
+    _check(G, runs, edges, min_bins=8)
+
+
+def test_819200_particle_disk_first_20_yr_match_the_oracle():
+    G = _load("trajectory_256x16x200_20yr.json")
+    edges, runs = _gpu_runs(G)
+    _check(G, runs, edges, min_bins=12)
