@@ -12,7 +12,16 @@ synthetic growth/fragmentation-balance state (workloads.midrun_state).  The
 working set (about 100 MB) is below the 129 MB L2, so a 512 MB buffer is
 written between timed steps and each step is timed alone with CUDA events.
 
+The same line carries the other configurations of the metric as records
+beside the benchmark number: "batched64" (64 independent disks in one
+context, 28.5 M particles), "stress" (1024 x 32 cells x 400 particles,
+alpha = 1e-2, v_frag = 1 m/s), both from mid-run states, and "full_run" (the
+benchmark disk evolved from its all-monomer initial state for 1e4 yr).  The
+collide kernel is reported against the FP32 ALU peak and against the
+shared-memory bandwidth measured in the same run (mcd_probe_peaks).
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--no-extra] [--full-run-yr Y] [--peaks]
 
 Under torchrun each rank runs its own independent disk (seed + rank): the work
 shards by disk with no data-path collective (weak scaling); the collective is
@@ -39,6 +48,8 @@ FLOPS_PER_ENTRY = 60          # FP32 flops of one kernel entry + rate weight (FM
 REGRID_BYTES = 92             # algorithmic bytes per particle per regrid
 TRANSPORT_BYTES = 44          # algorithmic bytes per particle per transport
 SMS, FP32_LANES = 152, 128
+SMEM_BYTES_PER_EVENT_SWARM = 60   # shared-memory bytes per event and swarm of the cell (two scans, row/column i)
+SMEM_BYTES_PER_ENTRY = 52         # shared-memory bytes per rate-matrix entry of a build (48-B swarm cache + 4-B dv)
 
 
 def peaks():
@@ -108,6 +119,27 @@ class ClockSampler:
                 "window_ms": 1e3 * (self.t1 - self.t0) if self.t0 is not None and self.t1 else None}
 
 
+def probe_peaks(stream=None) -> dict:
+    """This GPU's shared-memory read bandwidth and FP32/FP64 FMA throughput,
+    measured by the library's microbenchmarks (mcd_probe_peaks)."""
+    from paper_2507_21239_gb300 import mcd
+    return mcd.mcd_probe_peaks(stream)
+
+
+def collide_smem_bytes(n_c, ev_c) -> float:
+    """Algorithmic shared-memory bytes of one collide over cells of n_c swarms
+    with ev_c events each: every rate-matrix entry of a full build reads one
+    swarm cache and one dv (SMEM_BYTES_PER_ENTRY); a build at the start and
+    one every 4 n events; and per event ~60 n bytes (the two scans over the row
+    sums and row i, row i read, the new row and column written, the row-sum
+    updates and the caches read)."""
+    n = np.asarray(n_c, np.float64)
+    ev = np.asarray(ev_c, np.float64)
+    live = n > 0
+    builds = 1.0 + np.floor(ev[live] / (4.0 * n[live]))
+    return float(np.sum(SMEM_BYTES_PER_ENTRY * n[live] ** 2 * builds + SMEM_BYTES_PER_EVENT_SWARM * n[live] * ev[live]))
+
+
 def measured_traffic(name: str):
     """DRAM bytes per launch recorded from an ncu capture (profiles/traffic.json),
     or None when the kernel's source changed since the capture."""
@@ -121,6 +153,14 @@ def measured_traffic(name: str):
         return float(rec["bytes_per_launch"])
     except Exception:
         return None
+
+
+def smi_index(local: int) -> int:
+    """nvidia-smi's index of this process's GPU (CUDA_VISIBLE_DEVICES mapped)."""
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    if vis and vis.split(",")[0].strip().isdigit():
+        return int(vis.split(",")[local].strip())
+    return local
 
 
 def dist_env():
@@ -238,8 +278,9 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def timed_steps(mcd, d, dt, K, stream, flush, trace=True):
-    """K steps, each timed alone with CUDA events after an L2 flush."""
+def timed_steps(mcd, d, dt, K, stream, flush, trace=True, on_step=None):
+    """K steps, each timed alone with CUDA events after an L2 flush; on_step(k),
+    if given, runs after step k has finished, outside its timed interval."""
     import torch
     times, phases = [], []
     for k in range(K):
@@ -254,7 +295,43 @@ def timed_steps(mcd, d, dt, K, stream, flush, trace=True):
         times.append(e0.elapsed_time(e1))
         if trace:
             phases.append(mcd.mcd_trace_read(d.ctx))
+        if on_step is not None:
+            on_step(k)
     return np.array(times), np.array(phases) if phases else None
+
+
+def cell_loads(mcd, d, grids):
+    """Every cell's swarm count and events in the last collide, over all disks."""
+    ns, evs = [], []
+    for k, g in enumerate(grids):
+        C = g[0] * g[1]
+        off = np.zeros(C + 1, np.int64)
+        mcd.mcd_get_cells(d.ctx, k, off, None, None)
+        ev = np.zeros(C, np.int64)
+        mcd.mcd_get_cell_events(d.ctx, k, ev)
+        ns.append(np.diff(off))
+        evs.append(ev)
+    return np.concatenate(ns), np.concatenate(evs)
+
+
+def collide_rooflines(n_c, ev_c, n_steps, collide_ms, pk, fp32_unit_peak):
+    """The collide kernel against the FP32 ALU peak (unit counts x clock) and
+    against the measured shared-memory bandwidth; n_c, ev_c per cell and step
+    (arrays of shape steps x cells), collide_ms the mean phase time."""
+    entries = float(np.sum(n_c * (n_c + 1) / 2 + n_c * ev_c)) / n_steps
+    sm_bytes = sum(collide_smem_bytes(n_c[k], ev_c[k]) for k in range(n_steps)) / n_steps
+    t = collide_ms * 1e-3
+    alu = {"bound": "alu", "achieved": entries * FLOPS_PER_ENTRY / t / 1e12, "peak": fp32_unit_peak,
+           "unit": "TFLOP/s", "traffic": measured_traffic("k_collide<float>"), "kernel": "k_collide<float>",
+           "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock (MEASURED_PEAKS.json)",
+           "work": f"{FLOPS_PER_ENTRY} flop x {entries:.4g} kernel entries per step"}
+    smem = {"bound": "smem", "achieved": sm_bytes / t / 1e9, "peak": pk["smem_gbs"], "unit": "GB/s",
+            "traffic": None, "kernel": "k_collide<float>",
+            "peak_source": "measured in this run (mcd_probe_peaks shared-memory read loop)",
+            "work": f"{sm_bytes:.4g} algorithmic shared-memory bytes per step"}
+    for x in (alu, smem):
+        x["frac"] = x["achieved"] / x["peak"] if x["peak"] else None
+    return alu, smem
 
 
 def run_ours(args):
@@ -294,12 +371,11 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    gpu_index = local
-    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
-    if vis and vis.split(",")[0].strip().isdigit():
-        gpu_index = int(vis.split(",")[local].strip())
+    gpu_index = smi_index(local)
+    loads = []  # (swarms, events) per cell of every timed step: the collide's algorithmic work
     with ClockSampler(gpu_index) as clk:
-        times, phases = timed_steps(mcd, d, dt, args.steps, stream, flush)
+        times, phases = timed_steps(mcd, d, dt, args.steps, stream, flush,
+                                    on_step=lambda k: loads.append(cell_loads(mcd, d, [grid])))
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -311,25 +387,23 @@ def run_ours(args):
     total_ms, events = aggregate(total_ms, events, device=dev)
     value = events / (total_ms * 1e-3)
     yr_per_s = args.steps * args.dt_yr / (total_ms * 1e-3)
-    # cell populations for the algorithmic flop count of the collide kernel
-    off = np.zeros(grid[0] * grid[1] + 1, np.int64)
-    mcd.mcd_get_cells(d.ctx, 0, off, None, None)
-    n_c = np.diff(off).astype(np.float64)
     ev_step = (st1.events - st0.events) / args.steps
     ph = phases.mean(axis=0)  # regrid, order, collide, transport [ms]
     hbm, mhz, src = peaks()
+    pk = probe_peaks(stream)
     fp32_peak = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12  # TFLOP/s
-    entries = float(np.sum(n_c * (n_c + 1) / 2) + n_c.mean() * ev_step)
-    coll = {"bound": "alu", "achieved": entries * FLOPS_PER_ENTRY / (ph[2] * 1e-3) / 1e12, "peak": fp32_peak,
-            "unit": "TFLOP/s", "traffic": measured_traffic("k_collide<float>"), "kernel": "k_collide<float>"}
+    n_c = np.array([x[0] for x in loads], np.float64)
+    ev_c = np.array([x[1] for x in loads], np.float64)
+    coll, coll_smem = collide_rooflines(n_c, ev_c, args.steps, ph[2], pk, fp32_peak)
     reg = {"bound": "hbm", "achieved": REGRID_BYTES * N / (ph[0] * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-           "traffic": measured_traffic("regrid"), "kernel": "regrid (k_regrid_keys, k_radix_*, k_zone)"}
+           "traffic": measured_traffic("regrid"), "kernel": "regrid (k_regrid_keys, k_radix_*, k_zone)",
+           "peak_source": src}
     tra = {"bound": "hbm", "achieved": TRANSPORT_BYTES * N / (ph[3] * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-           "traffic": measured_traffic("k_transport<true>"), "kernel": "k_transport<true>"}
-    for x in (coll, reg, tra):
+           "traffic": measured_traffic("k_transport<true>"), "kernel": "k_transport<true>", "peak_source": src}
+    for x in (reg, tra):
         x["frac"] = x["achieved"] / x["peak"]
-        x["peak_source"] = src
     dom = max(((ph[2], coll), (ph[0], reg), (ph[3], tra)), key=lambda a: a[0])[1]
+    classes = mcd.mcd_get_collide_classes(d.ctx)
     d.close()
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -342,8 +416,14 @@ def run_ours(args):
                       "l2": f"{args.flush_mb} MB buffer written between timed steps; each step timed alone",
                       "graph": "step replayed as one CUDA graph", "parallelism": f"{world} independent disks"},
            "phases_ms": {"regrid": ph[0], "order": ph[1], "collide": ph[2], "transport": ph[3]},
-           "roofline": dom, "roofline_all": {"collide": coll, "regrid": reg, "transport": tra},
-           "gpu_launches": int(launches), "events_per_step": ev_step}
+           "roofline": dom,
+           "roofline_all": {"collide": coll, "collide_smem": coll_smem, "regrid": reg, "transport": tra},
+           "peaks_probe": {k: pk[k] for k in ("smem_gbs", "fp32_tflops", "fp64_tflops", "sm_count", "sm_clock_mhz",
+                                              "l2_bytes", "smem_per_sm_bytes")},
+           "collide_classes": [{k: c[k] for k in ("n_lo", "n_hi", "cells", "threads", "swarms_per_thread", "store",
+                                                  "control_warp", "persistent", "trials")} for c in classes],
+           "gpu_launches": int(launches), "events_per_step": ev_step,
+           "heaviest_cell_events": int(ev_c.max(axis=1).mean()) if ev_c.size else 0}
 
     if rank == 0 and not args.no_fp64:
         # ---- plain FP64 path on the same state --------------------------------
@@ -406,57 +486,158 @@ def run_ours(args):
                                "single_core": {"value": ev1 / el1, "unit": UNIT, "cores": 1,
                                                "sample": f"{steps1} full oracle step(s), {el1:.1f} s"}}
     out["clocks"] = clk.summary()
+    if rank == 0 and world == 1 and not args.no_extra:
+        # the other configurations of the metric, each in its own context:
+        # the 64-disk batch and the stress disk (mid-run states), and the
+        # benchmark disk's whole evolution from its initial state
+        out["batched64"] = measure_batched(args, stream, flush, pk, fp32_peak)
+        out["stress"] = measure_single(args, "stress_1024x32x400", stream, flush, pk, fp32_peak)
+    if rank == 0 and world == 1 and args.full_run_yr > 0:
+        out["full_run"] = measure_full_run(args, stream)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def run_batched(args):
-    """The 64-disk batch (workloads.batched_disks) in one context: mixed path,
-    one mid-run state per disk, whole-batch events/s over timed steps.  A
-    measurement of that configuration, not the benchmark line."""
+def measure_context(name, params, grids, states, seed, args, stream, flush, pk, fp32_peak, steps, warmup):
+    """One mixed-precision context of several disks (params, grids; mid-run
+    states m, r, z per disk) stepped `warmup` times untimed and `steps` times
+    timed (each step alone, after an L2 flush): whole-context events/s,
+    phases, launches, the collide's rooflines, the tuned cell classes."""
     import torch
-    from paper_2507_21239_gb300 import build as B, mcd, workloads as W
-    torch.cuda.set_device(0)
-    B.build()
-    disks = W.batched_disks()
-    params = [x["params"] for x in disks]
-    grids = [(x["n_r"], x["n_z"], x["per_cell"]) for x in disks]
-    stream = torch.cuda.Stream()
-    flush = torch.empty(max(args.flush_mb, 1) << 20, dtype=torch.uint8, device="cuda")
-    d = mcd.Disk(params, grids, seed=0, prec="mixed", stream=stream)
-    for k, g in enumerate(grids):
-        m, r, z = W.midrun_state(params[k], g[0] * g[1] * g[2], seed=k)
+    from paper_2507_21239_gb300 import mcd, workloads as W
+    d = mcd.Disk(params, grids, seed=seed, prec="mixed", stream=stream)
+    for k, (m, r, z) in enumerate(states):
         p = d.particles(k)
         mcd.mcd_set_particles(d.ctx, k, m, p["M"], r, z, p["id"])
     dt = args.dt_yr * W.YR
     mcd.mcd_trace(d.ctx, True)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         mcd.mcd_step(d.ctx, dt)
     torch.cuda.synchronize()
-    events = lambda: sum(d.stats(k).events for k in range(len(disks)))
+    events = lambda: sum(d.stats(k).events for k in range(len(grids)))
     ev0, l0 = events(), mcd.mcd_get_launch_count(d.ctx)
-    with ClockSampler(0) as clk:
-        times, phases = timed_steps(mcd, d, dt, args.steps, stream, flush)
+    loads = []
+    with ClockSampler(smi_index(0)) as clk:
+        times, phases = timed_steps(mcd, d, dt, steps, stream, flush,
+                                    on_step=lambda k: loads.append(cell_loads(mcd, d, grids)))
     torch.cuda.synchronize()
     ev = events() - ev0
     launches = mcd.mcd_get_launch_count(d.ctx) - l0
     status = mcd.mcd_sync(d.ctx)
     total_ms = float(times.sum())
     ph = phases.mean(axis=0)
+    n_c = np.array([x[0] for x in loads], np.float64)
+    ev_c = np.array([x[1] for x in loads], np.float64)
+    alu, smem = collide_rooflines(n_c, ev_c, steps, ph[2], pk, fp32_peak)
+    classes = mcd.mcd_get_collide_classes(d.ctx)
     n = sum(g[0] * g[1] * g[2] for g in grids)
-    out = {"metric": METRIC, "value": ev / (total_ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-           "dtype": "f32+f64 (mixed)", "data": "synthetic", "status": mcd.mcd_strerror(status),
-           "config": {"workload": "batched64", "disks": len(disks), "particles": n,
-                      "cells": sum(g[0] * g[1] for g in grids), "dt_yr": args.dt_yr,
-                      "state": "workloads.midrun_state per disk (seed = disk)"},
-           "events_per_step": ev / args.steps,
+    out = {"workload": name, "value": ev / (total_ms * 1e-3), "unit": UNIT, "steps": steps, "warmup": warmup,
+           "ms_per_step": total_ms / steps, "disk_yr_per_s": len(grids) * steps * args.dt_yr / (total_ms * 1e-3),
+           "status": mcd.mcd_strerror(status), "disks": len(grids), "particles": n,
+           "cells": sum(g[0] * g[1] for g in grids), "dt_yr": args.dt_yr, "events_per_step": ev / steps,
+           "heaviest_cell_events": int(ev_c.max(axis=1).mean()) if ev_c.size else 0,
            "phases_ms": {"regrid": ph[0], "order": ph[1], "collide": ph[2], "transport": ph[3]},
-           "gpu_launches": launches, "clocks": clk.summary()}
+           "roofline_collide": alu, "roofline_collide_smem": smem, "gpu_launches": int(launches),
+           "collide_classes": [{k: c[k] for k in ("n_lo", "n_hi", "cells", "threads", "swarms_per_thread", "store",
+                                                  "control_warp", "persistent", "trials")} for c in classes],
+           "state": "workloads.midrun_state per disk (seed = disk)", "clocks": clk.summary()}
     d.close()
+    return out
+
+
+def measure_batched(args, stream, flush, pk, fp32_peak):
+    """The 64-disk batch (workloads.batched_disks: alpha x v_frag grid, 32-512
+    radial zones and 50-400 particles per cell per disk, 8 vertical cells) in
+    one context."""
+    from paper_2507_21239_gb300 import workloads as W
+    disks = W.batched_disks()
+    params = [x["params"] for x in disks]
+    grids = [(x["n_r"], x["n_z"], x["per_cell"]) for x in disks]
+    states = [W.midrun_state(params[k], g[0] * g[1] * g[2], seed=k) for k, g in enumerate(grids)]
+    return measure_context("batched64", params, grids, states, 0, args, stream, flush, pk, fp32_peak,
+                           args.extra_steps, args.extra_warmup)
+
+
+def measure_single(args, name, stream, flush, pk, fp32_peak):
+    """One of workloads.WORKLOADS (a single disk) from its mid-run state."""
+    from paper_2507_21239_gb300 import workloads as W
+    wl = W.WORKLOADS[name]
+    grid = (wl["n_r"], wl["n_z"], wl["per_cell"])
+    state = W.midrun_state(wl["params"], grid[0] * grid[1] * grid[2], seed=wl["seed"])
+    return measure_context(name, [wl["params"]], [grid], [state], wl["seed"], args, stream, flush, pk, fp32_peak,
+                           args.extra_steps, args.extra_warmup)
+
+
+def measure_full_run(args, stream):
+    """The 819,200-particle disk evolved from its initial state (all monomers,
+    z ~ N(0, H_g)) for args.full_run_yr years in 1-yr steps, mixed path, as
+    one stream of graph replays: wall time, simulated years per second, events
+    per step over time, and the mass bookkeeping at the end."""
+    import torch
+    from paper_2507_21239_gb300 import mcd, workloads as W
+    wl = W.WORKLOADS["disk2d_256x16x200"]
+    grid = (wl["n_r"], wl["n_z"], wl["per_cell"])
+    d = mcd.Disk(wl["params"], grid, seed=wl["seed"], prec="mixed", stream=stream)
+    M0 = float(d.particles()["M"].sum())
+    dt = args.dt_yr * W.YR
+    n_steps = int(round(args.full_run_yr / args.dt_yr))
+    mark = max(1, n_steps // 10)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0.record(stream)
+    trace, prev_ev, prev_k = [], 0, 0
+    with ClockSampler(smi_index(0)) as clk:
+        for k in range(1, n_steps + 1):
+            mcd.mcd_step(d.ctx, dt)
+            if k % mark == 0 or k == n_steps:
+                ev = d.stats().events  # (synchronises: a few per run)
+                trace.append({"yr": k * args.dt_yr, "events_per_step": (ev - prev_ev) / (k - prev_k)})
+                prev_ev, prev_k = ev, k
+    e1.record(stream)
+    e1.synchronize()
+    wall = time.perf_counter() - t0
+    dev_ms = e0.elapsed_time(e1)
+    st = d.stats()
+    status = mcd.mcd_sync(d.ctx)
+    x = d.particles()
+    alive = np.isfinite(x["r"])
+    mass_err = abs(float(x["M"][alive].sum()) + st.accreted_mass - M0) / M0
+    m = x["m"][alive]
+    out = {"workload": "disk2d_256x16x200 from the initial state", "sim_yr": n_steps * args.dt_yr,
+           "steps": n_steps, "wall_s": wall, "device_s": dev_ms * 1e-3, "sim_yr_per_s": n_steps * args.dt_yr / wall,
+           "events": int(st.events), "events_per_s": st.events / wall, "status": mcd.mcd_strerror(status),
+           "events_per_step_trace": trace, "mass_rel_err": mass_err, "alive": int(alive.sum()),
+           "m_max_g": float(m.max()) if m.size else None,
+           "note": "wall time of the whole run including the host's graph launches and a few status reads",
+           "clocks": clk.summary()}
+    d.close()
+    return out
+
+
+def run_batched(args):
+    """The 64-disk batch alone: one JSON line (not the benchmark line)."""
+    import torch
+    from paper_2507_21239_gb300 import build as B
+    torch.cuda.set_device(0)
+    B.build()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(max(args.flush_mb, 1) << 20, dtype=torch.uint8, device="cuda")
+    _, mhz, _ = peaks()
+    out = measure_batched(args, stream, flush, probe_peaks(stream), SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12)
+    out["metric"] = METRIC
     print(json.dumps(out), flush=True)
+
+
+def run_peaks(args):
+    import torch
+    from paper_2507_21239_gb300 import build as B
+    torch.cuda.set_device(0)
+    B.build()
+    print(json.dumps({"peaks_probe": probe_peaks(torch.cuda.current_stream())}), flush=True)
 
 
 def main():
@@ -475,8 +656,16 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched64 and stress records")
+    ap.add_argument("--extra-steps", type=int, default=5, help="timed steps of the batched64 and stress records")
+    ap.add_argument("--extra-warmup", type=int, default=3)
+    ap.add_argument("--full-run-yr", type=float, default=1e4,
+                    help="years of the full_run record (the benchmark disk from its initial state); 0 skips it")
+    ap.add_argument("--peaks", action="store_true", help="print the microbenchmarked peaks only")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.peaks:
+        run_peaks(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched64":
         run_batched(args)

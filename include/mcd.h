@@ -140,9 +140,17 @@ typedef struct mcd_ctx mcd_ctx;
                                    must then leave room for it); 0 (default): block sums of the row sums'
                                    leading parts, relative error below 10 ulp, formed afresh each event */
 #define MCD_OPT_AUTOTUNE 16     /* 1 (default): before its first collide the context times the candidate
-                                   variants of each cell class (swarms per thread, dv-matrix store) on the
-                                   class's largest cells and keeps the fastest (mcd_get_collide_classes);
-                                   setting it to 1 again repeats the trial at the next collide */
+                                   variants of each cell class (swarms per thread, control warp, dv-matrix
+                                   store) on the class's largest cells and keeps the fastest
+                                   (mcd_get_collide_classes); setting it to 1 again repeats the trial at the
+                                   next collide */
+#define MCD_OPT_CONTROL_WARP 18 /* MCD_MIXED: 1 runs every class with a control warp (one warp keeps the row
+                                   sums in registers and makes both choices with warp-wide scans; one worker
+                                   thread per swarm forms the rows); 0 the block variants (every thread
+                                   holds its swarms' row sums, block-wide scans); -1 (default) the timed
+                                   trial decides per class, unless MCD_OPT_SWARMS_PER_THREAD is set.  The
+                                   trajectories differ from the block variants' at the level of FP32
+                                   rounding in the choice scans */
 
 /*
  * Bytes of device workspace needed for n_disks disks at precision prec.
@@ -271,17 +279,19 @@ int mcd_get_total_rates(mcd_ctx *ctx, int32_t disk, double *Rtot, int32_t where)
  * largest cells).  Host memory; up to cap records, *count the number of
  * classes.  This is the implementation's scheduling, not the paper's method.
  */
+#define MCD_MAX_TRIALS 12
 typedef struct {
     int32_t n_lo, n_hi;          /* particles per cell of the class's disks */
     int64_t cells;               /* cells in the class */
     int32_t threads;             /* threads per cell */
-    int32_t swarms_per_thread;   /* 1 or 2 */
+    int32_t swarms_per_thread;   /* 1 or 2 (the control-warp variant: 1 per worker thread) */
     int32_t store;               /* dv matrix: 0 row i recomputed, 1 shared memory, 2 workspace */
     int32_t persistent;          /* persistent CTAs take cells by atomic ticket */
+    int32_t control_warp;        /* 1: the control-warp variant (MCD_OPT_CONTROL_WARP) */
     int32_t tuned;               /* 1: chosen by the timed trial */
-    int32_t n_trials;            /* candidates timed (at most 8) */
-    int32_t trial_swarms[8], trial_store[8];
-    float trial_us_per_event[8]; /* the trial's time per event [us] */
+    int32_t n_trials;            /* candidates timed (at most MCD_MAX_TRIALS) */
+    int32_t trial_swarms[MCD_MAX_TRIALS], trial_store[MCD_MAX_TRIALS], trial_control_warp[MCD_MAX_TRIALS];
+    float trial_us_per_event[MCD_MAX_TRIALS]; /* the trial's time per event [us] */
 } mcd_collide_class;
 int mcd_get_collide_classes(mcd_ctx *ctx, mcd_collide_class *out, int32_t cap, int32_t *count);
 

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmcd.so")
 SOURCES = ["mcd_capi.cu", "mcd_collide.cu", "mcd_collide_f32s1.cu", "mcd_collide_f32s2.cu", "mcd_collide_f32s1x.cu",
-           "mcd_collide_f32s2x.cu", "mcd_collide_f64.cu",
+           "mcd_collide_f32s2x.cu", "mcd_collide_f64.cu", "mcd_collide_f32ws4.cu", "mcd_collide_f32ws10.cu",
            "mcd_regrid.cu", "mcd_transport.cu", "mcd_noalloc.cu", "mcd_diag.cu", "mcd_step.cu", "mcd_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]

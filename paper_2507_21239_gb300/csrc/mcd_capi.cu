@@ -699,13 +699,14 @@ int mcd_get_collide_classes(mcd_ctx *c, mcd_collide_class *out, int32_t cap, int
         o.n_lo = k.n_lo;
         o.n_hi = k.n_hi;
         o.cells = k.cells;
-        collide_shape(c, q, &o.swarms_per_thread, &o.store, &o.threads);
+        collide_shape(c, q, &o.swarms_per_thread, &o.store, &o.threads, &o.control_warp);
         o.persistent = c->persistent;
         o.tuned = k.tuned;
         o.n_trials = k.n_trials;
-        for (int t = 0; t < k.n_trials && t < 8; ++t) {
+        for (int t = 0; t < k.n_trials && t < MCD_MAX_TRIALS; ++t) {
             o.trial_swarms[t] = k.trial_S[t];
             o.trial_store[t] = k.trial_store[t];
+            o.trial_control_warp[t] = k.trial_ws[t];
             o.trial_us_per_event[t] = k.trial_us[t];
         }
     }
@@ -800,6 +801,10 @@ int mcd_set_option(mcd_ctx *c, int32_t key, double v)
         c->spt = (int32_t)v;
         break;
     case MCD_OPT_PERSISTENT: c->persistent = v != 0.0; break;
+    case MCD_OPT_CONTROL_WARP:
+        if (!(v == -1.0 || v == 0.0 || (v == 1.0 && c->prec == MCD_MIXED))) return MCD_EINVAL;
+        c->control_warp = (int32_t)v;
+        break;
     case MCD_OPT_EXACT_TOTAL: c->exact_total = v != 0.0; break;
     case MCD_OPT_AUTOTUNE:
         c->autotune = v != 0.0;

@@ -3,10 +3,11 @@
 // timed trial that picks each class's variant, and the probes.  The kernels
 // themselves are in mcd_collide.cuh, instantiated per (precision, swarms per
 // thread, exact total) in mcd_collide_f32s1.cu, mcd_collide_f32s2.cu,
-// mcd_collide_f32s1x.cu, mcd_collide_f32s2x.cu and mcd_collide_f64.cu.
+// mcd_collide_f32s1x.cu, mcd_collide_f32s2x.cu and mcd_collide_f64.cu, and the
+// control-warp variants in mcd_collide_ws.cuh (mcd_collide_f32ws.cu).
 #include <algorithm>
 
-#include "mcd_collide.cuh"
+#include "mcd_collide_ws.cuh"
 
 namespace mcd {
 
@@ -228,6 +229,27 @@ static cudaError_t variant(int op, int S, int store, bool ramp, bool tracer, boo
     }
 }
 
+// the control-warp variants: swarms per control lane for cells of up to n
+// swarms (0: none fits)
+static int ws_pl(int n)
+{
+    for (int pl : {4, 7, 10, 16})
+        if (32 * pl >= n) return pl;
+    return 0;
+}
+
+static cudaError_t ws_variant(int op, int pl, int store, bool ramp, bool tracer, unsigned grid, int nthr, size_t smem,
+                              cudaStream_t st, const CollideArgs *A, int *out)
+{
+    switch (pl) {
+    case 4: return collide_ws_variant<4>(op, store, ramp, tracer, grid, nthr, smem, st, A, out);
+    case 7: return collide_ws_variant<7>(op, store, ramp, tracer, grid, nthr, smem, st, A, out);
+    case 10: return collide_ws_variant<10>(op, store, ramp, tracer, grid, nthr, smem, st, A, out);
+    case 16: return collide_ws_variant<16>(op, store, ramp, tracer, grid, nthr, smem, st, A, out);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 // the store a class can use: 1 needs the FP32 shared matrix to fit, 2 a
 // reserved workspace matrix; otherwise recompute
 template <class T>
@@ -241,15 +263,41 @@ static int usable_store(const CollideClass &k, int want)
 struct ClassLaunch {
     int S, store, nthr;
     size_t smem;
+    int ws, pl;  // the control-warp variant and its swarms per control lane
 };
+
+// whether class k runs the control-warp variant: MCD_MIXED without the exact
+// total or a thread count, forced by the option (cw 0 or 1), else the class's
+// choice unless swarms per thread are set
+template <class T>
+static bool class_ws(const CollideClass &k, int threads, int spt, int cw, int exact)
+{
+    if (sizeof(T) == 8 || threads || exact || !ws_pl(k.n_hi)) return false;
+    if (cw >= 0) return cw == 1;
+    return !spt && k.ws;
+}
 
 // the launch shape of class k: the options' swarms per thread and store when
 // set (spt, dv_matrix >= 0), else the class's chosen ones
 template <class T>
 static ClassLaunch class_launch(const CollideClass &k, int threads, int spt, int dv_matrix, int exclusive, int tracer,
-                                int exact, int smem_optin)
+                                int exact, int smem_optin, int ws)
 {
     ClassLaunch L;
+    L.ws = ws;
+    L.pl = ws ? ws_pl(k.n_hi) : 0;
+    if (ws) {
+        L.S = 1;
+        L.store = usable_store<T>(k, dv_matrix >= 0 ? dv_matrix : k.store);
+        L.nthr = 32 + round32(k.n_hi);
+        L.smem = collide_ws_smem_bytes(L.pl, tracer != 0, L.store, k.rows, k.W);
+        if (L.store == 1 && L.smem > (size_t)smem_optin) {
+            L.store = usable_store<T>(k, 2);
+            L.smem = collide_ws_smem_bytes(L.pl, tracer != 0, L.store, k.rows, k.W);
+        }
+        if (exclusive && k.n_hi > 64 && L.smem < kExclusiveSmem) L.smem = kExclusiveSmem;
+        return L;
+    }
     L.S = (sizeof(T) == 8 || threads) ? 1 : (spt ? spt : k.S);
     // (FP32: one swarm per thread leaves no room for the helper warp above 480 swarms)
     if (sizeof(T) == 4 && !threads && block_threads<T>(class_threads(k.n_hi, 1), exact) > kMaxCell) L.S = 2;
@@ -271,15 +319,25 @@ template <class T>
 static ClassLaunch class_launch(const mcd_ctx *cx, const CollideClass &k)
 {
     return class_launch<T>(k, cx->threads, cx->spt, cx->dv_matrix, cx->exclusive, cx->tracer, cx->exact_total,
-                           cx->smem_optin);
+                           cx->smem_optin, class_ws<T>(k, cx->threads, cx->spt, cx->control_warp, cx->exact_total));
 }
 
-void collide_shape(const mcd_ctx *c, int q, int32_t *S, int32_t *store, int32_t *threads)
+void collide_shape(const mcd_ctx *c, int q, int32_t *S, int32_t *store, int32_t *threads, int32_t *control_warp)
 {
     const ClassLaunch L = c->prec == MCD_MIXED ? class_launch<float>(c, c->cls[q]) : class_launch<double>(c, c->cls[q]);
     *S = L.S;
     *store = L.store;
     *threads = L.nthr;
+    *control_warp = L.ws;
+}
+
+// one launch-time operation (variant op codes) of a class launch shape
+template <class T>
+static cudaError_t launch_op(int op, const ClassLaunch &L, bool ramp, bool tracer, bool exact, unsigned grid,
+                             cudaStream_t st, const CollideArgs *A, int *out)
+{
+    if (L.ws) return ws_variant(op, L.pl, L.store, ramp, tracer, grid, L.nthr, L.smem, st, A, out);
+    return variant<T>(op, L.S, L.store, ramp, tracer, exact, grid, L.nthr, L.smem, st, A, out);
 }
 
 template <class T>
@@ -340,9 +398,11 @@ static cudaError_t collide_impl(mcd_ctx *cx, int from_state, double t_end)
     for (int q = 0; q < ncls && e == cudaSuccess; ++q) {
         const CollideClass &k = cx->cls[q];
         const ClassLaunch L = class_launch<T>(cx, k);
-        if (L.nthr - block_threads<T>(0, cx->exact_total) < (k.n_hi + L.S - 1) / L.S || L.nthr > kMaxCell / L.S ||
-            L.smem > (size_t)cx->smem_optin)
+        if (L.ws ? (L.nthr - 32 < k.n_hi || 32 * L.pl < k.n_hi || L.nthr > 32 + 32 * L.pl)
+                 : (L.nthr - block_threads<T>(0, cx->exact_total) < (k.n_hi + L.S - 1) / L.S ||
+                    L.nthr > kMaxCell / L.S))
             return cudaErrorInvalidValue;
+        if (L.smem > (size_t)cx->smem_optin) return cudaErrorInvalidValue;
         cudaStream_t st = q == 0 ? cx->stream : cx->cls_stream[q];
         if (q > 0 && (e = cudaStreamWaitEvent(st, cx->cls_fork, 0)) != cudaSuccess) return e;
         A.queue = (cx->lpt ? cx->queue : cx->queue_static) + k.qoff;
@@ -354,14 +414,14 @@ static cudaError_t collide_impl(mcd_ctx *cx, int from_state, double t_end)
         A.qhead = nullptr;
         if (cx->persistent) {
             int per_sm = 0;
-            e = variant<T>(3, L.S, L.store, cx->ramp != 0, cx->tracer != 0, exact, 0, L.nthr, L.smem, st, &A, &per_sm);
+            e = launch_op<T>(3, L, cx->ramp != 0, cx->tracer != 0, exact, 0, st, &A, &per_sm);
             if (e != cudaSuccess) return e;
             const int64_t cap = (int64_t)std::max(per_sm, 1) * cx->n_sm;
             grid = (unsigned)std::min<int64_t>(k.cells, cap);
             A.qhead = cx->qheads + q;
             if ((e = cudaMemsetAsync(A.qhead, 0, sizeof(int32_t), st)) != cudaSuccess) return e;
         }
-        e = variant<T>(0, L.S, L.store, cx->ramp != 0, cx->tracer != 0, exact, grid, L.nthr, L.smem, st, &A, nullptr);
+        e = launch_op<T>(0, L, cx->ramp != 0, cx->tracer != 0, exact, grid, st, &A, nullptr);
         cx->launches += 1;
         if (e == cudaSuccess && q > 0) {
             e = cudaEventRecord(cx->cls_join[q], st);
@@ -393,6 +453,19 @@ static cudaError_t prepare_impl(mcd_ctx *c)
                 if (dyn <= 0) return cudaErrorInvalidValue;
                 if ((e = variant<T>(1, S, store, false, false, exact, 0, 0, (size_t)dyn, nullptr, nullptr,
                                     nullptr)) != cudaSuccess)
+                    return e;
+                smin = std::min(smin, dyn);
+            }
+    if (sizeof(T) == 4)  // the control-warp variants
+        for (int pl : {4, 7, 10, 16})
+            for (int store = 0; store <= 2; ++store) {
+                int st = 0;
+                if ((e = ws_variant(2, pl, store, false, false, 0, 0, 0, nullptr, nullptr, &st)) != cudaSuccess)
+                    return e;
+                const int dyn = optin - st;
+                if (dyn <= 0) return cudaErrorInvalidValue;
+                if ((e = ws_variant(1, pl, store, false, false, 0, 0, (size_t)dyn, nullptr, nullptr, nullptr)) !=
+                    cudaSuccess)
                     return e;
                 smin = std::min(smin, dyn);
             }
@@ -446,20 +519,30 @@ static cudaError_t tune_impl(mcd_ctx *c)
     bool cc_done = false;
     for (size_t q = 0; q < c->cls.size() && e == cudaSuccess; ++q) {
         CollideClass &k = c->cls[q];
-        std::vector<std::pair<int, int>> cand;
-        for (int S = 1; S <= (sizeof(T) == 4 ? 2 : 1); ++S) {
-            if (c->spt && S != c->spt) continue;
-            if (S == 2 && class_threads(k.n_hi, 2) >= class_threads(k.n_hi, 1)) continue;  // no fewer warps
-            if (S == 1 && block_threads<T>(class_threads(k.n_hi, 1), c->exact_total) > kMaxCell) continue;
-            for (int store : {1, 2, 0}) {
-                if (c->dv_matrix >= 0 && usable_store<T>(k, c->dv_matrix) != store) continue;
-                if (usable_store<T>(k, store) != store) continue;
-                cand.push_back({S, store});
+        struct Cand {
+            int S, store, ws;
+        };
+        std::vector<Cand> cand;
+        // the control-warp variant: when the options leave it open (or ask for it)
+        const bool ws_ok = sizeof(T) == 4 && !c->threads && !c->exact_total && ws_pl(k.n_hi) &&
+                           (c->control_warp == 1 || (c->control_warp < 0 && !c->spt));
+        for (int ws = 0; ws <= 1; ++ws) {
+            if (ws ? !ws_ok : c->control_warp == 1 && ws_ok) continue;
+            for (int S = 1; S <= (sizeof(T) == 4 && !ws ? 2 : 1); ++S) {
+                if (!ws && c->spt && S != c->spt) continue;
+                if (!ws && S == 2 && class_threads(k.n_hi, 2) >= class_threads(k.n_hi, 1)) continue;  // no fewer warps
+                if (!ws && S == 1 && block_threads<T>(class_threads(k.n_hi, 1), c->exact_total) > kMaxCell) continue;
+                for (int store : {1, 2, 0}) {
+                    if (c->dv_matrix >= 0 && usable_store<T>(k, c->dv_matrix) != store) continue;
+                    if (usable_store<T>(k, store) != store) continue;
+                    cand.push_back({S, store, ws});
+                }
             }
         }
         if (cand.empty()) continue;
-        k.S = cand[0].first;
-        k.store = cand[0].second;
+        k.S = cand[0].S;
+        k.store = cand[0].store;
+        k.ws = cand[0].ws;
         if (cand.size() < 2 || !c->autotune) continue;
         // the class's largest cells
         std::vector<int32_t> pick;
@@ -495,9 +578,9 @@ static cudaError_t tune_impl(mcd_ctx *c)
         k.n_trials = 0;
         float best = 3.0e38f;
         for (const auto &cs : cand) {
-            const ClassLaunch L = class_launch<T>(k, c->threads, cs.first, cs.second, c->exclusive, c->tracer,
-                                                  c->exact_total, c->smem_optin);
-            if (L.S != cs.first || L.store != cs.second) continue;  // (the launch would not run this candidate)
+            const ClassLaunch L = class_launch<T>(k, c->threads, cs.S, cs.store, c->exclusive, c->tracer,
+                                                  c->exact_total, c->smem_optin, cs.ws);
+            if (L.S != cs.S || L.store != cs.store) continue;  // (the launch would not run this candidate)
             if (L.smem > (size_t)c->smem_optin) continue;
             A.dvg = L.store == 2 ? k.dvg : nullptr;
             float ms[4] = {};
@@ -506,8 +589,8 @@ static cudaError_t tune_impl(mcd_ctx *c)
                 if (e == cudaSuccess && A.q) e = cudaMemcpyAsync(A.q, c->q[b], 8 * c->N, cudaMemcpyDeviceToDevice, st);
                 if (e == cudaSuccess) e = cudaEventRecord(t0, st);
                 if (e == cudaSuccess)
-                    e = variant<T>(0, L.S, L.store, c->ramp != 0, c->tracer != 0, sizeof(T) == 4 && c->exact_total,
-                                   (unsigned)pick.size(), L.nthr, L.smem, st, &A, nullptr);
+                    e = launch_op<T>(0, L, c->ramp != 0, c->tracer != 0, sizeof(T) == 4 && c->exact_total,
+                                     (unsigned)pick.size(), st, &A, nullptr);
                 c->launches += 1;
                 if (e == cudaSuccess) e = cudaEventRecord(t1, st);
                 if (e == cudaSuccess) e = cudaEventSynchronize(t1);
@@ -518,14 +601,16 @@ static cudaError_t tune_impl(mcd_ctx *c)
             const float us = 1e3f * ms[2] / kTrialEvents;
             if (k.n_trials < kMaxTrials) {
                 k.trial_us[k.n_trials] = us;
-                k.trial_S[k.n_trials] = cs.first;
-                k.trial_store[k.n_trials] = cs.second;
+                k.trial_S[k.n_trials] = cs.S;
+                k.trial_store[k.n_trials] = cs.store;
+                k.trial_ws[k.n_trials] = cs.ws;
                 ++k.n_trials;
             }
             if (us < best) {
                 best = us;
-                k.S = cs.first;
-                k.store = cs.second;
+                k.S = cs.S;
+                k.store = cs.store;
+                k.ws = cs.ws;
             }
         }
         k.tuned = 1;

@@ -225,7 +225,7 @@ constexpr int kCellKBytes = 384;
 // thread and dv-matrix store, and its own launch on its own stream, so that
 // heavy chains of different classes run side by side.
 constexpr int kMaxClasses = 5;
-constexpr int kMaxTrials = 8;
+constexpr int kMaxTrials = 12;
 struct CollideClass {
     int32_t n_lo = 0, n_hi = 0;  // particles per cell of the class's disks
     int64_t cells = 0, qoff = 0; // its cells and their first queue position (class-major queue)
@@ -234,9 +234,10 @@ struct CollideClass {
     int32_t reserve = 0;         // the plan reserves the class's matrices in the workspace
     void *dvg = nullptr;         // those matrices (null: not reserved)
     int32_t S = 1, store = 0;    // swarms per thread; 0 recompute row i, 1 shared matrix, 2 workspace matrix
+    int32_t ws = 0;              // 1: the control-warp variant (one worker thread per swarm)
     int32_t tuned = 0, n_trials = 0;
     float trial_us[kMaxTrials] = {};  // per candidate: trial time per event on the class's largest cells
-    int32_t trial_S[kMaxTrials] = {}, trial_store[kMaxTrials] = {};
+    int32_t trial_S[kMaxTrials] = {}, trial_store[kMaxTrials] = {}, trial_ws[kMaxTrials] = {};
 };
 
 // row width of a circulant half matrix for cells of up to n swarms: at least
@@ -323,6 +324,7 @@ struct mcd_ctx {
     int32_t use_graph = 1, dump_R = 0, lpt = 1, threads = 0, exclusive = 1;
     int32_t dv_matrix = -1;  // -1 chosen by the trial; 0 recompute; 1 stored (shared, else workspace); 2 workspace
     int32_t spt = 0;         // swarms per thread: 0 chosen by the trial, 1 or 2
+    int32_t control_warp = -1;  // MCD_MIXED: 1 the control-warp variant, 0 the block variants, -1 the trial decides
     int32_t persistent = 0;  // 1: persistent collide CTAs take cells by atomic ticket
     int32_t autotune = 1;    // 1: the first collide times the candidate variants of each class
     int32_t exact_total = 0; // MCD_MIXED: the compensated total rate (one helper warp per cell)
@@ -362,7 +364,8 @@ cudaError_t launch_adaptive_dt(mcd_ctx *c);  // writes dt into the device state
 std::vector<unsigned long long> adaptive_dt_rest(int32_t n_disks);
 cudaError_t prepare_collide(mcd_ctx *c);
 cudaError_t tune_collide(mcd_ctx *c);  // the timed trial (once per context, before the first collide)
-void collide_shape(const mcd_ctx *c, int q, int32_t *S, int32_t *store, int32_t *threads);  // class q's launch
+void collide_shape(const mcd_ctx *c, int q, int32_t *S, int32_t *store, int32_t *threads,
+                   int32_t *control_warp);  // class q's launch
 int plan_classes(const mcd_grid *g, int32_t nd, int32_t prec, std::vector<CollideClass> &cls,
                  std::vector<int32_t> &disk_class);
 size_t class_matrix_bytes(const CollideClass &k, int32_t prec);  // 0: no workspace matrix for the class

@@ -20,7 +20,8 @@ MCD_HOST, MCD_DEVICE = 0, 1
 (MCD_OPT_MAX_EVENTS, MCD_OPT_CAP_STOPS, MCD_OPT_REBUILD_EVERY, MCD_OPT_USE_GRAPH, MCD_OPT_DUMP_R,
  MCD_OPT_LOG_CELL, MCD_OPT_LPT, MCD_OPT_THREADS, MCD_OPT_EXCLUSIVE, MCD_OPT_DV_MATRIX, MCD_OPT_TRACER,
  MCD_OPT_DT_MAX, MCD_OPT_COURANT, MCD_OPT_SWARMS_PER_THREAD, MCD_OPT_PERSISTENT, MCD_OPT_AUTOTUNE,
- MCD_OPT_EXACT_TOTAL) = range(1, 18)
+ MCD_OPT_EXACT_TOTAL, MCD_OPT_CONTROL_WARP) = range(1, 19)
+MCD_MAX_TRIALS = 12
 PREC = {"fp64": MCD_FP64, "mixed": MCD_MIXED}
 
 
@@ -59,8 +60,10 @@ class mcd_stats(C.Structure):
 class mcd_collide_class(C.Structure):
     _fields_ = [("n_lo", C.c_int32), ("n_hi", C.c_int32), ("cells", C.c_int64), ("threads", C.c_int32),
                 ("swarms_per_thread", C.c_int32), ("store", C.c_int32), ("persistent", C.c_int32),
-                ("tuned", C.c_int32), ("n_trials", C.c_int32), ("trial_swarms", C.c_int32 * 8),
-                ("trial_store", C.c_int32 * 8), ("trial_us_per_event", C.c_float * 8)]
+                ("control_warp", C.c_int32), ("tuned", C.c_int32), ("n_trials", C.c_int32),
+                ("trial_swarms", C.c_int32 * MCD_MAX_TRIALS), ("trial_store", C.c_int32 * MCD_MAX_TRIALS),
+                ("trial_control_warp", C.c_int32 * MCD_MAX_TRIALS),
+                ("trial_us_per_event", C.c_float * MCD_MAX_TRIALS)]
 
 
 class mcd_peaks(C.Structure):
@@ -232,8 +235,10 @@ def mcd_get_collide_classes(ctx: int) -> list[dict]:
         t = k.n_trials
         out.append({"n_lo": k.n_lo, "n_hi": k.n_hi, "cells": k.cells, "threads": k.threads,
                     "swarms_per_thread": k.swarms_per_thread, "store": k.store, "persistent": k.persistent,
-                    "tuned": k.tuned, "trials": [{"swarms_per_thread": k.trial_swarms[q], "store": k.trial_store[q],
-                                                  "us_per_event": k.trial_us_per_event[q]} for q in range(t)]})
+                    "control_warp": k.control_warp, "tuned": k.tuned,
+                    "trials": [{"swarms_per_thread": k.trial_swarms[q], "store": k.trial_store[q],
+                                "control_warp": k.trial_control_warp[q],
+                                "us_per_event": k.trial_us_per_event[q]} for q in range(t)]})
     return out
 
 

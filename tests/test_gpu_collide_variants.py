@@ -79,27 +79,31 @@ def test_five_classes_follow_the_oracle_event_for_event():
     d.close()
 
 
-def test_persistent_ctas_equal_one_cta_per_cell_on_the_64_disk_batch():
+@pytest.mark.parametrize("control_warp", [0, 1])
+def test_persistent_ctas_equal_one_cta_per_cell_on_the_64_disk_batch(control_warp):
     """Mixed path, the 64-disk batch (28.5 M particles, classes from 50 to 400
     particles per cell): one step from each disk's mid-run state with
     persistent CTAs gives the masses, row sums and event counts of one CTA per
     cell, bit for bit (the random numbers are keyed by disk, cell and event,
-    not by the CTA that runs the cell)."""
+    not by the CTA that runs the cell); for the block variants and for the
+    control-warp variant."""
     disks = W.batched_disks()
     params = [x["params"] for x in disks]
     grids = [(x["n_r"], x["n_z"], x["per_cell"]) for x in disks]
     states = [W.midrun_state(params[k], g[0] * g[1] * g[2], seed=k) for k, g in enumerate(grids)]
     out = []
+    shape = ((mcd.MCD_OPT_CONTROL_WARP, 1),) if control_warp else ((mcd.MCD_OPT_SWARMS_PER_THREAD, 1),)
     for persistent in (0, 1):
         d = mcd.Disk(params, grids, seed=0, prec="mixed")
-        for key, v in ((mcd.MCD_OPT_PERSISTENT, persistent), (mcd.MCD_OPT_SWARMS_PER_THREAD, 1),
-                       (mcd.MCD_OPT_DV_MATRIX, 1), (mcd.MCD_OPT_DUMP_R, 1)):
+        for key, v in ((mcd.MCD_OPT_PERSISTENT, persistent), (mcd.MCD_OPT_DV_MATRIX, 1),
+                       (mcd.MCD_OPT_DUMP_R, 1)) + shape:
             mcd.mcd_set_option(d.ctx, key, v)
         for k, (m, r, z) in enumerate(states):
             p = d.particles(k)
             mcd.mcd_set_particles(d.ctx, k, m, p["M"], r, z, p["id"])
         d.step(YR)
         assert mcd.mcd_sync(d.ctx) == mcd.MCD_OK
+        assert all(k["control_warp"] == control_warp for k in mcd.mcd_get_collide_classes(d.ctx))
         res = []
         for k in (0, 17, 40, 63):
             R = np.zeros(grids[k][0] * grids[k][1] * grids[k][2])
@@ -117,8 +121,9 @@ def test_persistent_ctas_equal_one_cta_per_cell_on_the_64_disk_batch():
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_timed_trial_keeps_the_fastest_candidate(prec):
     """Before the first collide each class times its candidates (mixed: one or
-    two swarms per thread x shared or no matrix; FP64: workspace or no matrix)
-    and runs the fastest; the step then conserves mass."""
+    two swarms per thread, or the control warp, x shared or no matrix; FP64:
+    workspace or no matrix) and runs the fastest; the step then conserves
+    mass."""
     P = W.benchmark_disk()
     grid = (8, 4, 200)
     d = mcd.Disk(P, grid, seed=1, prec=prec)
@@ -129,13 +134,16 @@ def test_timed_trial_keeps_the_fastest_candidate(prec):
     assert mcd.mcd_sync(d.ctx) == mcd.MCD_OK
     (k,) = mcd.mcd_get_collide_classes(d.ctx)
     assert k["tuned"] == 1
-    want = {(1, 1), (1, 0), (2, 1), (2, 0)} if prec == "mixed" else {(1, 2), (1, 0)}
-    got = {(t["swarms_per_thread"], t["store"]) for t in k["trials"]}
+    want = ({(1, 1, 0), (1, 0, 0), (2, 1, 0), (2, 0, 0), (1, 1, 1), (1, 0, 1)} if prec == "mixed"
+            else {(1, 2, 0), (1, 0, 0)})
+    got = {(t["swarms_per_thread"], t["store"], t["control_warp"]) for t in k["trials"]}
     assert got == want
     best = min(k["trials"], key=lambda t: t["us_per_event"])
     assert all(t["us_per_event"] > 0 for t in k["trials"])
-    assert (k["swarms_per_thread"], k["store"]) == (best["swarms_per_thread"], best["store"])
-    assert k["threads"] == (224 if k["swarms_per_thread"] == 1 else 128)  # one thread per swarm or per two
+    assert (k["swarms_per_thread"], k["store"], k["control_warp"]) == (
+        best["swarms_per_thread"], best["store"], best["control_warp"])
+    # one thread per swarm, per two, or a control warp and one worker thread per swarm
+    assert k["threads"] == (256 if k["control_warp"] else 224 if k["swarms_per_thread"] == 1 else 128)
     x = d.particles()
     alive = np.isfinite(x["r"])
     M0 = p["M"].sum()
@@ -175,7 +183,7 @@ def _plain_scan_total(x, spt):
     return float(a[-1])
 
 
-@pytest.mark.parametrize("spt", [1, 2])
+@pytest.mark.parametrize("spt", [1, 2, 0])
 def test_total_rate_plain_and_compensated(spt):
     """Cells of 400 swarms whose masses span 1e-12 .. 1 g (row sums over ~12
     decades), mixed path, stopped after the rebuild.  By default the total
@@ -186,7 +194,9 @@ def test_total_rate_plain_and_compensated(spt):
     MCD_OPT_EXACT_TOTAL it is the compensated sum: within 2e-9 of the exact
     (fsum) total of the kernel's own row sums in every cell, a bound that the
     plain sum misses in most cells.  Both equal the oracle's FP64 total of the
-    same cell to 1e-5."""
+    same cell to 1e-5.  spt 0: the control-warp variant, whose plain total is
+    the one warp's scan of 16 row sums per lane (the exact total then runs the
+    block variant with its helper warp)."""
     P = W.benchmark_disk()
     grid = (2, 4, 400)
     N = grid[0] * grid[1] * grid[2]
@@ -200,8 +210,9 @@ def test_total_rate_plain_and_compensated(spt):
         p = d.particles()
         mcd.mcd_set_particles(d.ctx, 0, m, p["M"], r, z, p["id"])
         mcd.mcd_regrid(d.ctx)
+        shape = ((mcd.MCD_OPT_SWARMS_PER_THREAD, spt),) if spt else ((mcd.MCD_OPT_CONTROL_WARP, -1 if exact else 1),)
         for key, v in ((mcd.MCD_OPT_MAX_EVENTS, 0), (mcd.MCD_OPT_CAP_STOPS, 1), (mcd.MCD_OPT_DUMP_R, 1),
-                       (mcd.MCD_OPT_SWARMS_PER_THREAD, spt), (mcd.MCD_OPT_EXACT_TOTAL, exact)):
+                       (mcd.MCD_OPT_EXACT_TOTAL, exact)) + shape:
             mcd.mcd_set_option(d.ctx, key, v)
         mcd.mcd_collide(d.ctx, 1.0)
         assert mcd.mcd_sync(d.ctx) == mcd.MCD_OK
@@ -221,7 +232,7 @@ def test_total_rate_plain_and_compensated(spt):
         Rc = R[off[c]:off[c + 1]]
         assert len(Rc) == 400 and np.array_equal(Rc, out[0][0][off[c]:off[c + 1]])
         exact = math.fsum(Rc)
-        plain = _plain_scan_total(Rc, spt)
+        plain = _plain_scan_total(Rc, spt if spt else 16)
         assert out[0][1][c] == plain, (c, out[0][1][c], plain)  # the kernel's plain sum, bit for bit
         assert abs(plain / exact - 1) <= 10 * 2.0**-24
         assert abs(out[1][1][c] / exact - 1) <= 2e-9, (c, out[1][1][c], exact)

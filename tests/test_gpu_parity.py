@@ -490,10 +490,10 @@ def test_graph_replay_equals_direct_launches(prec):
     b.close()
 
 
-DV_CASES = [(mcd.MCD_FP64, 1), (mcd.MCD_MIXED, 1), (mcd.MCD_MIXED, 2)]
+DV_CASES = [(mcd.MCD_FP64, 1), (mcd.MCD_MIXED, 1), (mcd.MCD_MIXED, 2), (mcd.MCD_MIXED, 0)]
 
 
-@pytest.mark.parametrize("prec,spt", DV_CASES, ids=["fp64", "mixed_s1", "mixed_s2"])
+@pytest.mark.parametrize("prec,spt", DV_CASES, ids=["fp64", "mixed_s1", "mixed_s2", "mixed_control_warp"])
 @pytest.mark.parametrize("grid,reb", [((8, 4, 30), 0), ((4, 2, 57), 7), ((1, 1, 200), 0), ((2, 2, 224), 13),
                                       ((1, 2, 312), 0), ((2, 1, 400), 11)])
 def test_dv_matrix_equals_recompute(grid, reb, prec, spt):
@@ -503,7 +503,9 @@ def test_dv_matrix_equals_recompute(grid, reb, prec, spt):
     at every event, for one and two swarms per thread.  Mid-run state, so
     sticking, erosion and fragmentation all occur; reb > 0 also runs the full
     rebuilds from stored entries; 312 swarms is a class whose matrix just fits
-    in shared memory, 400 one that takes the workspace matrix."""
+    in shared memory, 400 one that takes the workspace matrix.  spt 0 runs the
+    control-warp variant (one warp holds the row sums and chooses, one worker
+    thread per swarm)."""
     P = W.benchmark_disk()
     N = grid[0] * grid[1] * grid[2]
     m, r, z = W.midrun_state(P, N, seed=3)
@@ -515,13 +517,16 @@ def test_dv_matrix_equals_recompute(grid, reb, prec, spt):
         d = _make_ctx(P, grid, seed=4, prec=prec)
         p = d.particles()
         mcd.mcd_set_particles(d.ctx, 0, m, p["M"], r, z, p["id"])
-        for key, v in ((mcd.MCD_OPT_DV_MATRIX, mat), (mcd.MCD_OPT_REBUILD_EVERY, reb), (mcd.MCD_OPT_DUMP_R, 1),
-                       (mcd.MCD_OPT_SWARMS_PER_THREAD, spt)):
+        opts = [(mcd.MCD_OPT_DV_MATRIX, mat), (mcd.MCD_OPT_REBUILD_EVERY, reb), (mcd.MCD_OPT_DUMP_R, 1)]
+        opts += [(mcd.MCD_OPT_SWARMS_PER_THREAD, spt)] if spt else [(mcd.MCD_OPT_CONTROL_WARP, 1)]
+        for key, v in opts:
             mcd.mcd_set_option(d.ctx, key, v)
         for _ in range(2):
             d.step(YR)
         assert mcd.mcd_sync(d.ctx) == mcd.MCD_OK
-        store = mcd.mcd_get_collide_classes(d.ctx)[0]["store"]
+        k0 = mcd.mcd_get_collide_classes(d.ctx)[0]
+        assert k0["control_warp"] == (spt == 0)
+        store = k0["store"]
         R = np.zeros(N)
         mcd.mcd_get_rates(d.ctx, 0, R)
         out.append((d.particles(), d.stats().events, R, store))

@@ -8,7 +8,8 @@ from its JSON fixtures: per disk the per-bin sums (M, M m, M m^2, M m^3,
 count) over 16 logarithmic radial bins and the per-bin histogram of log10 m
 (0.2 dex), the accreted and initial swarm mass.  The GPU runs the same disks
 (same seed and disk index, hence the same initial draw) in one batched
-context.
+context, once with the collide's block variants and once with its
+control-warp variant.
 
 Per bin that holds particles in every run of both sides:
 * the across-seed means of the bin mass and of the mass-weighted moments
@@ -49,13 +50,14 @@ def _load(name):
         return json.load(f)
 
 
-def _gpu_runs(G):
+def _gpu_runs(G, control_warp):
     c = G["case"]
     wl = W.WORKLOADS[c["workload"]]
     P, grid = wl["params"], (wl["n_r"], wl["n_z"], wl["per_cell"])
     edges = np.asarray(G["edges"])
     nd = c["disks"]
     d = mcd.Disk([P] * nd, [grid] * nd, seed=c["seed"], prec="mixed")
+    mcd.mcd_set_option(d.ctx, mcd.MCD_OPT_CONTROL_WARP, control_warp)
     M0 = [d.particles(k)["M"].sum() for k in range(nd)]
     for _ in range(c["steps"]):
         d.step(c["dt_yr"] * W.YR)
@@ -141,13 +143,21 @@ def _check(G, runs, edges, min_bins):
     return worst, pvals
 
 
-def test_32_seeds_through_1e4_yr_match_the_oracle_in_distribution():
+# the collide's block variants (every thread holds its swarms' row sums) and
+# its control-warp variant (one warp holds them all) choose with scans of
+# different summation order: both are held to the bar
+VARIANTS = pytest.mark.parametrize("control_warp", [0, 1], ids=["block", "control_warp"])
+
+
+@VARIANTS
+def test_32_seeds_through_1e4_yr_match_the_oracle_in_distribution(control_warp):
     G = _load("trajectory_16x4x100_1e4yr.json")
-    edges, runs = _gpu_runs(G)
+    edges, runs = _gpu_runs(G, control_warp)
     _check(G, runs, edges, min_bins=8)
 
 
-def test_819200_particle_disk_first_20_yr_match_the_oracle():
+@VARIANTS
+def test_819200_particle_disk_first_20_yr_match_the_oracle(control_warp):
     G = _load("trajectory_256x16x200_20yr.json")
-    edges, runs = _gpu_runs(G)
+    edges, runs = _gpu_runs(G, control_warp)
     _check(G, runs, edges, min_bins=12)
