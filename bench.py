@@ -204,6 +204,18 @@ def make_state(args, ctx_or_none, rank):
     return P, grid, N, m, r, z
 
 
+def pin_variant(mcd, d, spec: str):
+    """Pin the mixed collide's variant instead of the timed trial's choice
+    (for profiling one kernel): "S,store" (swarms per thread 1 or 2; dv store
+    0 recompute, 1 shared memory, 2 workspace) or "cw,store" (control warp)."""
+    shape, store = spec.split(",")
+    if shape == "cw":
+        mcd.mcd_set_option(d.ctx, mcd.MCD_OPT_CONTROL_WARP, 1)
+    else:
+        mcd.mcd_set_option(d.ctx, mcd.MCD_OPT_SWARMS_PER_THREAD, int(shape))
+    mcd.mcd_set_option(d.ctx, mcd.MCD_OPT_DV_MATRIX, int(store))
+
+
 def cpu_model() -> str:
     """The host CPU: lscpu's model name, else /proc/cpuinfo's, else the architecture."""
     import platform
@@ -358,6 +370,8 @@ def run_ours(args):
         d = mcd.Disk(P, grid, seed=seed, prec=prec, stream=stream)
         p = d.particles()
         mcd.mcd_set_particles(d.ctx, 0, m, p["M"], r, z, p["id"])
+        if prec == "mixed" and args.collide_variant:
+            pin_variant(mcd, d, args.collide_variant)
         return d, p
 
     # ---- mixed precision, device-resident inputs ---------------------------
@@ -632,6 +646,86 @@ def run_batched(args):
     print(json.dumps(out), flush=True)
 
 
+def _oracle_disk_run(job):
+    """One oracle disk evolution (spawned worker, one thread): (events, seconds)."""
+    workload, seed, disk, dt_yr, steps = job
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_2507_21239_gb300 import workloads as W
+    wl = W.WORKLOADS[workload]
+    P, grid = wl["params"], (wl["n_r"], wl["n_z"], wl["per_cell"])
+    s = oracle.init_disk(P, grid[0] * grid[1] * grid[2], seed=seed, disk=disk)
+    t0 = time.perf_counter()
+    st = oracle.run(P, grid[0], grid[1], s, 0.0, dt_yr * W.YR, 0, steps, seed=seed, disk=disk, nthreads=1)
+    return int(s.events), time.perf_counter() - t0, int(st)
+
+
+def run_oracle_runs(args):
+    """Full runs timed end to end: the 0D constant-kernel cell (200 swarms to
+    t = 100) and the 16 x 4 x 100 disk through 1e4 yr (32 seeds, 50-yr steps),
+    the oracle on every host core (one disk per process) and per core, the GPU
+    (mixed and FP64, the seeds batched in one context) beside it."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    from paper_2507_21239_gb300 import workloads as W
+    cores = os.cpu_count() or 1
+    seeds, dt_yr, steps = args.oracle_seeds, 50.0, 200
+    jobs = [("disk2d_16x4x100", 7, d, dt_yr, steps) for d in range(seeds)]
+    # the pool starts (spawn) before this process touches the GPU
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(min(cores, seeds)) as pool:
+        res = pool.map(_oracle_disk_run, jobs)
+    wall = time.perf_counter() - t0
+    ev = sum(r[0] for r in res)
+    per_core = [r[0] / r[1] for r in res]
+    out = {"host": {"cpu": cpu_model(), "cores": cores}}
+    out["disk2d_16x4x100_1e4yr"] = {
+        "seeds": seeds, "sim_yr_per_disk": dt_yr * steps, "oracle_all_cores": {
+            "wall_s": wall, "events": ev, "events_per_s": ev / wall, "disk_yr_per_s": seeds * dt_yr * steps / wall,
+            "processes": min(cores, seeds), "status": sorted({r[2] for r in res})},
+        "oracle_one_core": {"events_per_s_median": float(np.median(per_core)),
+                            "disk_yr_per_s_median": float(np.median([dt_yr * steps / r[1] for r in res])),
+                            "seconds_per_disk_median": float(np.median([r[1] for r in res]))}}
+    P0 = W.constant_kernel_cell()
+    t0 = time.perf_counter()
+    st, m, ev0, _, _ = oracle.collide_cell(P0, 0.0, 0.0, 1.0, np.ones(200), np.full(200, 1.0 / 200), 0.0, 100.0,
+                                           0, 0, 0, 0)
+    el0 = time.perf_counter() - t0
+    out["0d_const_200_t100"] = {"oracle_one_core": {"seconds": el0, "events": ev0, "status": st,
+                                                    "mean_mass": float(m.mean())}}
+    # the GPU on the same runs
+    import torch
+    from paper_2507_21239_gb300 import build as B, mcd
+    torch.cuda.set_device(0)
+    B.build()
+    d = mcd.Disk(P0, (1, 1, 200), seed=0, prec="fp64")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mcd.mcd_collide(d.ctx, 100.0)
+    assert mcd.mcd_sync(d.ctx) == mcd.MCD_OK
+    el = time.perf_counter() - t0
+    out["0d_const_200_t100"]["gpu_fp64"] = {"seconds": el, "events": int(d.stats().events),
+                                           "mean_mass": float(d.particles()["m"].mean())}
+    d.close()
+    wl = W.WORKLOADS["disk2d_16x4x100"]
+    grid = (wl["n_r"], wl["n_z"], wl["per_cell"])
+    for prec, nd in (("mixed", seeds), ("fp64", seeds)):
+        d = mcd.Disk([wl["params"]] * nd, [grid] * nd, seed=7, prec=prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            mcd.mcd_step(d.ctx, dt_yr * W.YR)
+        status = mcd.mcd_sync(d.ctx)
+        el = time.perf_counter() - t0
+        evg = sum(d.stats(k).events for k in range(nd))
+        out["disk2d_16x4x100_1e4yr"]["gpu_" + prec] = {
+            "disks": nd, "wall_s": el, "events": evg, "events_per_s": evg / el, "disk_yr_per_s": nd * dt_yr * steps / el,
+            "status": mcd.mcd_strerror(status)}
+        d.close()
+    print(json.dumps({"oracle_runs": out}), flush=True)
+
+
 def run_peaks(args):
     import torch
     from paper_2507_21239_gb300 import build as B
@@ -662,8 +756,15 @@ def main():
     ap.add_argument("--full-run-yr", type=float, default=1e4,
                     help="years of the full_run record (the benchmark disk from its initial state); 0 skips it")
     ap.add_argument("--peaks", action="store_true", help="print the microbenchmarked peaks only")
+    ap.add_argument("--collide-variant", default=None,
+                    help='pin the mixed collide variant of the main line, "S,store" or "cw,store" (profiling)')
+    ap.add_argument("--oracle-runs", action="store_true",
+                    help="time the oracle's full runs (0D cell; the 16 x 4 x 100 disk through 1e4 yr) and the GPU beside it")
+    ap.add_argument("--oracle-seeds", type=int, default=32)
     args = ap.parse_args()
-    if args.peaks:
+    if args.oracle_runs:
+        run_oracle_runs(args)
+    elif args.peaks:
         run_peaks(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -99,6 +99,8 @@ size_t carve(mcd_ctx *c, void *base, Sizes &S, int32_t nd, int32_t prec)
     int64_t H = 256 * S.T;
     x->hist = cv.take<uint32_t>(H);
     x->scan_part = cv.take<uint32_t>(H / 4096 + 2);
+    x->rfix_longs = cv.take<int64_t>(S.N / (kRunShortMax + 1) + 1);
+    x->rfix_count = cv.take<int32_t>(2);
     x->cell_start = cv.take<int64_t>(S.C);
     x->cell_n = cv.take<int32_t>(S.C);
     x->cell_b = cv.take<double>(6 * S.C);

@@ -206,9 +206,14 @@ struct StepState {
     int64_t step;
 };
 
+// the r sort's fix-up: runs of equal upper key words longer than this are
+// listed (so a list of N / (kRunShortMax + 1) + 1 entries always suffices)
+constexpr int kRunShortMax = 64;
+
 // radix sort tile: 256 threads x 16 keys
 constexpr int kRadixThreads = 256, kRadixItems = 16, kRadixTile = kRadixThreads * kRadixItems;
 constexpr int kRadixBins = 256, kRadixPasses = 8;
+constexpr int kRadixUpperPasses = 4;  // the r sort runs the passes of the keys' upper four bytes
 
 // largest cell population the collide kernel takes (one thread per swarm)
 constexpr int kMaxCell = 512;
@@ -278,6 +283,9 @@ struct mcd_ctx {
     uint32_t *val[2] = {};
     uint32_t *hist = nullptr;      // [n_tiles * 256] in (disk, digit, tile) order
     uint32_t *scan_part = nullptr; // block partials of the histogram scan
+    int64_t *rfix_longs = nullptr; // the r sort's long runs of equal upper key words (first position each)
+    int32_t *rfix_count = nullptr; // [0] long runs listed, [1] the fix-up CTAs' ticket
+    int32_t n_sm_regrid = 0;       // SMs of the device (the long-run fix-up's grid)
 
     int64_t *cell_start = nullptr;  // global particle slot of each cell's first particle
     int32_t *cell_n = nullptr;

@@ -42,7 +42,9 @@ constexpr size_t kOffVal0 = align256(kOffKey1 + 8 * kNoAllocMax);
 constexpr size_t kOffVal1 = align256(kOffVal0 + 4 * kNoAllocMax);
 constexpr size_t kOffHist = align256(kOffVal1 + 4 * kNoAllocMax);
 constexpr size_t kOffPart = align256(kOffHist + 4 * 256 * kTiles);
-constexpr size_t kOffAlive = align256(kOffPart + 4 * kScanParts);
+constexpr size_t kOffLongs = align256(kOffPart + 4 * kScanParts);
+constexpr size_t kOffRfix = align256(kOffLongs + 8 * (kNoAllocMax / (mcd::kRunShortMax + 1) + 1));
+constexpr size_t kOffAlive = align256(kOffRfix + 8);
 constexpr size_t kOffStatus = align256(kOffAlive + 8);
 constexpr size_t kScratchBytes = align256(kOffStatus + 4);
 
@@ -136,6 +138,8 @@ extern "C" int mcd_regrid_noalloc(const mcd_disk_params *p, const mcd_grid *g, c
     c.val[1] = reinterpret_cast<uint32_t *>(s + kOffVal1);
     c.hist = reinterpret_cast<uint32_t *>(s + kOffHist);
     c.scan_part = reinterpret_cast<uint32_t *>(s + kOffPart);
+    c.rfix_longs = reinterpret_cast<int64_t *>(s + kOffLongs);
+    c.rfix_count = reinterpret_cast<int32_t *>(s + kOffRfix);
     c.n_alive = reinterpret_cast<int64_t *>(s + kOffAlive);
     c.status = reinterpret_cast<int32_t *>(s + kOffStatus);
     c.m[0] = const_cast<double *>(m);  // read only

@@ -11,15 +11,17 @@
 // GB300 design:
 //  1. keys: each particle's order-preserving 64-bit r key is written at
 //     position (disk offset + id), so a stable sort by r alone breaks ties by id;
-//  2. a segmented LSD radix sort, 8 passes of 8 bits, all disks in one launch
+//  2. a segmented LSD radix sort of the keys' upper four bytes (sign, exponent
+//     and 20 mantissa bits), 4 passes of 8 bits, all disks in one launch
 //     sequence (tiles never straddle disks; the histogram is laid out disk-major,
-//     digit, tile so one exclusive scan yields every scatter offset);
+//     digit, tile so one exclusive scan yields every scatter offset), then every
+//     run of equal upper words put in (r, id) order (k_rfix, k_rfix_long);
 //  3. one CTA per radial zone loads its (z, id) keys into shared memory, sorts
-//     them with a bitonic network that needs no padding (every compare is
-//     ascending, absent elements act as +inf), computes cell bounds with
-//     explicitly rounded FP64 operations (no fused multiply-add, so they are
-//     bit-identical to a plain CPU evaluation), and gathers the particle
-//     columns into cell order.
+//     them (radix on the upper words with the same run fix-up, or a bitonic
+//     network that needs no padding: every compare is ascending, absent
+//     elements act as +inf), computes cell bounds with explicitly rounded FP64
+//     operations (no fused multiply-add, so they are bit-identical to a plain
+//     CPU evaluation), and gathers the particle columns into cell order.
 #include <math.h>
 
 #include "mcd_internal.cuh"
@@ -310,16 +312,204 @@ __device__ __forceinline__ bool zless(const uint4 &a, const uint4 &b)
     return ka < kb || (ka == kb && a.z < b.z);
 }
 
+// Bitonic sort of el[0, n) in shared memory by (key, id) (zless); every
+// compare ascending, i < j, j < n (32-bit indices; strides are powers of two,
+// so / and % are shifts).  Pair p of a stage touches positions inside an
+// aligned block of 2^(lt+1); with nw warps each warp owns the aligned chunk of
+// 2^lwb positions whose pairs are p in [w 2^(lwb-1), (w+1) 2^(lwb-1)), so the
+// stages with lt < lwb need only the warp's own synchronisation.  blockDim.x
+// is a power-of-two multiple of 32; every thread of the block calls it.
+__device__ void block_bitonic(uint4 *el, int n)
+{
+    int lg = 0;
+    while ((1 << lg) < n) ++lg;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int lgw = 31 - __clz((int)(blockDim.x >> 5));
+    const int lwb = lg - lgw;
+    auto stage = [&](int ls, int lt, int p) {
+        const int stride = 1 << lt;
+        int i, j;
+        if (lt == ls - 1) {  // first step of a merge: mirror compare
+            const int blk = p >> lt, off = p & (stride - 1);
+            i = (blk << ls) + off;
+            j = (blk << ls) + (1 << ls) - 1 - off;
+        } else {
+            i = ((p >> lt) << (lt + 1)) + (p & (stride - 1));
+            j = i + stride;
+        }
+        if (j < n) {
+            const uint4 a = el[i], b = el[j];
+            if (zless(b, a)) {
+                el[i] = b;
+                el[j] = a;
+            }
+        }
+    };
+    for (int ls = 1; ls <= lg; ++ls) {         // merge size 2^ls
+        for (int lt = ls - 1; lt >= 0; --lt) {  // compare stride 2^lt
+            if (lt >= lwb) {  // pairs span warps
+                for (int p = threadIdx.x; p < (1 << (lg - 1)); p += blockDim.x) stage(ls, lt, p);
+                __syncthreads();
+            } else {
+                const int p1 = (w + 1) << (lwb - 1);
+                for (int p = (w << (lwb - 1)) + lane; p < p1; p += 32) stage(ls, lt, p);
+                __syncwarp();
+            }
+        }
+        // a merge that ended in warp-local stages is followed by a block barrier
+        // when the next merge opens with a cross-warp stage, and at the end
+        if (lwb >= 1 && (ls >= lwb || ls == lg)) __syncthreads();
+    }
+}
+
 constexpr int kZoneThreads = 512;  // two zones per SM
+
+// ---- the r sort's fix-up --------------------------------------------------------
+// The radix passes sort the r keys by their upper 32 bits only (sign, exponent
+// and 20 mantissa bits), stably, so positions with equal upper words hold their
+// keys in id order.  Each such run is then put in (full key, id) order: runs of
+// up to kRunShort by the thread at their start (insertion sort, stable, in
+// place), longer ones are listed for k_rfix_long.  Runs are disjoint and a
+// permutation inside a run leaves its upper words unchanged, so the threads'
+// run tests do not race with the sorts.  The removed particles' run (+inf) is
+// already in order.
+constexpr int kRunShort = kRunShortMax;
+
+__global__ void k_rfix(const DiskDev *disks, const int32_t *slot_disk, int64_t N, uint64_t *key, uint32_t *val,
+                       int64_t *longs, int32_t *n_long)
+{
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const DiskDev D = disks[slot_disk[s]];
+    const int64_t end = D.p_off + D.n0;
+    const uint32_t hi = (uint32_t)(key[s] >> 32);
+    if (hi == (uint32_t)(kInfKey >> 32)) return;
+    if (s + 1 >= end || (uint32_t)(key[s + 1] >> 32) != hi) return;
+    if (s > D.p_off && (uint32_t)(key[s - 1] >> 32) == hi) return;  // not the run's first position
+    int64_t e = s + 1;
+    while (e + 1 < end && e - s < kRunShort && (uint32_t)(key[e + 1] >> 32) == hi) ++e;
+    if (e - s + 1 > kRunShort) {
+        longs[atomicAdd(n_long, 1)] = s;  // (at most N / (kRunShort + 1) of them)
+        return;
+    }
+    for (int64_t i = s + 1; i <= e; ++i) {
+        const uint64_t k = key[i];
+        const uint32_t v = val[i];
+        int64_t j = i - 1;
+        while (j >= s && key[j] > k) {
+            key[j + 1] = key[j];
+            val[j + 1] = val[j];
+            --j;
+        }
+        key[j + 1] = k;
+        val[j + 1] = v;
+    }
+}
+
+// the listed long runs, one CTA each (taken by an atomic ticket): the run's
+// length, nothing to do when all its full keys are equal, else a bitonic sort
+// by (key, id) -- in shared memory up to kZoneCap positions, in place in
+// global memory beyond (inputs that put more than 14,336 particles within a
+// relative 2^-20 of one radius and not all at the same one)
+__global__ void __launch_bounds__(kZoneThreads) k_rfix_long(const DiskDev *disks, const int32_t *slot_disk,
+                                                           uint64_t *key, uint32_t *val, const uint32_t *id0,
+                                                           const int64_t *longs, const int32_t *n_long,
+                                                           int32_t *ticket)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint4 *el = reinterpret_cast<uint4 *>(smem_raw);
+    __shared__ int64_t s_sh;
+    __shared__ unsigned long long len_sh;
+    __shared__ int diff_sh;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int t = atomicAdd(ticket, 1);
+            s_sh = t < *n_long ? longs[t] : -1;
+        }
+        __syncthreads();
+        const int64_t s = s_sh;
+        if (s < 0) return;
+        const DiskDev D = disks[slot_disk[s]];
+        const int64_t end = D.p_off + D.n0;
+        const uint64_t k0 = key[s];
+        const uint32_t hi = (uint32_t)(k0 >> 32);
+        if (threadIdx.x == 0) {
+            len_sh = (unsigned long long)(end - s);
+            diff_sh = 0;
+        }
+        __syncthreads();
+        for (int64_t q = s + 1 + threadIdx.x; q < end; q += blockDim.x)
+            if ((uint32_t)(key[q] >> 32) != hi) {
+                atomicMin(&len_sh, (unsigned long long)(q - s));
+                break;
+            }
+        __syncthreads();
+        const int64_t L = (int64_t)len_sh;
+        for (int64_t q = threadIdx.x; q < L; q += blockDim.x)
+            if (key[s + q] != k0) diff_sh = 1;
+        __syncthreads();
+        if (!diff_sh) continue;  // equal keys: already in id order
+        if (L <= kZoneCap) {
+            for (int64_t q = threadIdx.x; q < L; q += blockDim.x) {
+                const uint64_t k = key[s + q];
+                const uint32_t v = val[s + q];  // (a source slot outside the disk: ids were not a permutation)
+                el[q] = make_uint4((uint32_t)k, (uint32_t)(k >> 32), id0[D.p_off + (v < D.n0 ? v : 0)], v);
+            }
+            __syncthreads();
+            block_bitonic(el, (int)L);
+            __syncthreads();
+            for (int64_t q = threadIdx.x; q < L; q += blockDim.x) {
+                key[s + q] = el_key(el[q]);
+                val[s + q] = el[q].w;
+            }
+        } else {
+            int lg = 0;
+            while ((1LL << lg) < L) ++lg;
+            auto idk = [&](int64_t q) {
+                const uint32_t v = val[s + q];
+                return id0[D.p_off + (v < D.n0 ? v : 0)];
+            };
+            for (int ls = 1; ls <= lg; ++ls)
+                for (int lt = ls - 1; lt >= 0; --lt) {
+                    const int64_t stride = 1LL << lt;
+                    for (int64_t p = threadIdx.x; p < (1LL << (lg - 1)); p += blockDim.x) {
+                        int64_t i, j;
+                        if (lt == ls - 1) {
+                            const int64_t blk = p >> lt, off = p & (stride - 1);
+                            i = (blk << ls) + off;
+                            j = (blk << ls) + (1LL << ls) - 1 - off;
+                        } else {
+                            i = ((p >> lt) << (lt + 1)) + (p & (stride - 1));
+                            j = i + stride;
+                        }
+                        if (j < L) {
+                            const uint64_t ka = key[s + i], kb = key[s + j];
+                            if (kb < ka || (kb == ka && idk(j) < idk(i))) {
+                                const uint32_t va = val[s + i];
+                                key[s + i] = kb;
+                                key[s + j] = ka;
+                                val[s + i] = val[s + j];
+                                val[s + j] = va;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+        }
+    }
+}
+
 constexpr int kZoneItems = 8;      // radix path: elements per lane, zones up to 16 x 32 x 8 = 4,096
 constexpr int kZoneRadixMax = (kZoneThreads / 32) * 32 * kZoneItems;
 constexpr int kTieRun = 64;  // longest run of equal heights the radix path orders by id in place
 
 // digit of element e in pass p: the first id_passes take the id's bytes, the
-// next eight the z key's (least significant first)
-__device__ __forceinline__ int zdigit(const uint4 &e, int p, int id_passes)
+// next ones the z key's from byte zb0 up (least significant first)
+__device__ __forceinline__ int zdigit(const uint4 &e, int p, int id_passes, int zb0)
 {
-    return p < id_passes ? (int)((e.z >> (8 * p)) & 255u) : (int)((el_key(e) >> (8 * (p - id_passes))) & 255u);
+    return p < id_passes ? (int)((e.z >> (8 * p)) & 255u)
+                         : (int)((el_key(e) >> (8 * (zb0 + p - id_passes))) & 255u);
 }
 
 // Stable LSD radix sort of a[0, n) by (z key, id): the id's bytes first, then
@@ -331,7 +521,7 @@ __device__ __forceinline__ int zdigit(const uint4 &e, int p, int id_passes)
 // (kZoneRadixScratch bytes after the two buffers), so the bitonic path keeps
 // the whole allocation for its one buffer.
 constexpr size_t kZoneRadixScratch = sizeof(uint16_t) * (kZoneThreads / 32) * kRadixBins + sizeof(uint32_t) * (kRadixBins + 8);
-__device__ uint4 *zone_radix(uint4 *a, uint4 *b, int n, int id_passes, unsigned char *scratch)
+__device__ uint4 *zone_radix(uint4 *a, uint4 *b, int n, int id_passes, int zb0, unsigned char *scratch)
 {
     uint16_t(*wcnt)[kRadixBins] = reinterpret_cast<uint16_t(*)[kRadixBins]>(scratch);
     uint32_t *doff = reinterpret_cast<uint32_t *>(scratch + sizeof(uint16_t) * (kZoneThreads / 32) * kRadixBins);
@@ -339,7 +529,7 @@ __device__ uint4 *zone_radix(uint4 *a, uint4 *b, int n, int id_passes, unsigned 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int per_warp = ((n + nw - 1) / nw + 31) & ~31;
     const unsigned below = (1u << lane) - 1u;
-    for (int p = 0; p < id_passes + 8; ++p) {
+    for (int p = 0; p < id_passes + 8 - zb0; ++p) {
         for (int q = threadIdx.x; q < nw * kRadixBins; q += blockDim.x) (&wcnt[0][0])[q] = 0;
         __syncthreads();
         uint32_t dr[kZoneItems];  // digit | rank << 9
@@ -347,7 +537,7 @@ __device__ uint4 *zone_radix(uint4 *a, uint4 *b, int n, int id_passes, unsigned 
         for (int it = 0; it < kZoneItems; ++it) {
             const int q = w * per_warp + it * 32 + lane;
             const bool ok = it * 32 < per_warp && q < n;
-            const int d = ok ? zdigit(a[q], p, id_passes) : 256;
+            const int d = ok ? zdigit(a[q], p, id_passes, zb0) : 256;
             const unsigned peers = digit_peers(d & 255, ok);
             const int leader = ok ? __ffs(peers) - 1 : lane;
             uint32_t old = 0;
@@ -461,31 +651,32 @@ __global__ void __launch_bounds__(kZoneThreads, 2) k_zone(ZoneArgs A)
     load();
     // (2) sort by (z, id)
     if (A.radix) {
-        // The z passes alone: a stable sort keeps equal z keys in their input
-        // (r) order, so each run of equal keys is then put in id order by the
-        // thread at its start (runs are disjoint, and swapping inside a run
-        // leaves every key of it unchanged).  A run longer than kTieRun redoes
-        // the sort with the id passes first.
+        // The upper four bytes of the z key alone (sign, exponent and 20
+        // mantissa bits): a stable sort by them, then each run of equal upper
+        // words is put in (full z key, id) order by the thread at its start
+        // (runs are disjoint; inside a run only the lower words and ids differ).
+        // Such runs are rare for continuous heights and short; a run longer
+        // than kTieRun redoes the sort with the id passes and all eight z passes.
         uint4 *const base = el;
         unsigned char *const scratch = reinterpret_cast<unsigned char *>(base + 2 * A.zcap);
-        el = zone_radix(base, base + A.zcap, (int)nk, 0, scratch);
+        el = zone_radix(base, base + A.zcap, (int)nk, 0, 4, scratch);
         __shared__ int long_run;
         if (threadIdx.x == 0) long_run = 0;
         __syncthreads();
         const int n32 = (int)nk;
         for (int q = threadIdx.x; q + 1 < n32; q += blockDim.x) {
-            const uint64_t kq = el_key(el[q]);
-            if (el_key(el[q + 1]) != kq || (q > 0 && el_key(el[q - 1]) == kq)) continue;
+            const uint32_t kq = el[q].y;
+            if (el[q + 1].y != kq || (q > 0 && el[q - 1].y == kq)) continue;
             int e = q + 1;
-            while (e + 1 < n32 && el_key(el[e + 1]) == kq) ++e;
+            while (e + 1 < n32 && el[e + 1].y == kq) ++e;
             if (e - q + 1 > kTieRun) {
                 long_run = 1;
                 continue;
             }
-            for (int i = q + 1; i <= e; ++i) {  // insertion sort of el[q..e] by id
+            for (int i = q + 1; i <= e; ++i) {  // insertion sort of el[q..e] by (z key, id)
                 const uint4 x = el[i];
                 int j = i - 1;
-                while (j >= q && el[j].z > x.z) {
+                while (j >= q && zless(x, el[j])) {
                     el[j + 1] = el[j];
                     --j;
                 }
@@ -496,55 +687,10 @@ __global__ void __launch_bounds__(kZoneThreads, 2) k_zone(ZoneArgs A)
         if (long_run) {
             el = base;
             load();
-            el = zone_radix(base, base + A.zcap, (int)nk, A.id_passes, scratch);
+            el = zone_radix(base, base + A.zcap, (int)nk, A.id_passes, 0, scratch);
         }
     } else {
-        // (2) bitonic sort by (z, id); every compare ascending, i < j, j < nk
-        //     (32-bit indices; strides are powers of two, so / and % are shifts).
-        //     Pair p of a stage touches positions inside an aligned block of
-        //     2^(lt+1); with nw warps each warp owns the aligned chunk of 2^lwb
-        //     positions whose pairs are p in [w 2^(lwb-1), (w+1) 2^(lwb-1)), so the
-        //     stages with lt < lwb need only the warp's own synchronisation.
-        const int nk32 = (int)nk;
-        int lg = 0;
-        while ((1 << lg) < nk32) ++lg;
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-        const int lgw = 31 - __clz((int)(blockDim.x >> 5));  // blockDim a power-of-two multiple of 32
-        const int lwb = lg - lgw;
-        auto stage = [&](int ls, int lt, int p) {
-            const int stride = 1 << lt;
-            int i, j;
-            if (lt == ls - 1) {  // first step of a merge: mirror compare
-                const int blk = p >> lt, off = p & (stride - 1);
-                i = (blk << ls) + off;
-                j = (blk << ls) + (1 << ls) - 1 - off;
-            } else {
-                i = ((p >> lt) << (lt + 1)) + (p & (stride - 1));
-                j = i + stride;
-            }
-            if (j < nk32) {
-                const uint4 a = el[i], b = el[j];
-                if (zless(b, a)) {
-                    el[i] = b;
-                    el[j] = a;
-                }
-            }
-        };
-        for (int ls = 1; ls <= lg; ++ls) {           // merge size 2^ls
-            for (int lt = ls - 1; lt >= 0; --lt) {    // compare stride 2^lt
-                if (lt >= lwb) {  // pairs span warps
-                    for (int p = threadIdx.x; p < (1 << (lg - 1)); p += blockDim.x) stage(ls, lt, p);
-                    __syncthreads();
-                } else {
-                    const int p1 = (w + 1) << (lwb - 1);
-                    for (int p = (w << (lwb - 1)) + lane; p < p1; p += 32) stage(ls, lt, p);
-                    __syncwarp();
-                }
-            }
-            // a merge that ended in warp-local stages is followed by a block barrier
-            // when the next merge opens with a cross-warp stage, and at the end
-            if (lwb >= 1 && (ls >= lwb || ls == lg)) __syncthreads();
-        }
+        block_bitonic(el, (int)nk);
     }
     // (3) bounds: radial edges of the zone, then one thread per cell
     __shared__ double rlo_s, rhi_s;
@@ -667,10 +813,15 @@ constexpr size_t kZoneSmemRadixMax = (size_t)kZoneRadixMax * sizeof(uint4) * 2 +
 constexpr size_t kZoneSmemBitonicMax = (size_t)kZoneCap * sizeof(uint4);
 constexpr size_t kZoneSmemMax = kZoneSmemRadixMax > kZoneSmemBitonicMax ? kZoneSmemRadixMax : kZoneSmemBitonicMax;
 
-cudaError_t prepare_zone(mcd_ctx *)
+cudaError_t prepare_zone(mcd_ctx *c)
 {
     cudaError_t e = cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterStage);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_rfix_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kZoneSmemBitonicMax);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&c->n_sm_regrid, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_zone, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kZoneSmemMax);
 }
 
@@ -684,7 +835,8 @@ cudaError_t launch_regrid(mcd_ctx *c)
                                       c->val[0], c->status);
     const int64_t H = 256 * c->n_tiles;
     const unsigned nsb = (unsigned)((H + kScanBlock - 1) / kScanBlock);
-    for (int pass = 0; pass < kRadixPasses; ++pass) {
+    // the upper four bytes of the keys (an even number of passes: the result is back in buffer 0)
+    for (int pass = kRadixPasses - kRadixUpperPasses; pass < kRadixPasses; ++pass) {
         const int shift = 8 * pass, src = pass & 1, dst = src ^ 1;
         k_radix_hist<<<(unsigned)c->n_tiles, kRadixThreads, 0, st>>>(c->d_disks, c->tile_disk, c->key[src], shift,
                                                                      c->hist);
@@ -694,7 +846,12 @@ cudaError_t launch_regrid(mcd_ctx *c)
             c->d_disks, c->tile_disk, c->key[src], c->val[src], c->key[dst], c->val[dst], shift, c->hist,
             c->scan_part);
     }
-    // kRadixPasses is even: the sorted keys are back in buffer 0
+    // runs of equal upper words into (key, id) order
+    cudaError_t e = cudaMemsetAsync(c->rfix_count, 0, 2 * sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    k_rfix<<<gN, 256, 0, st>>>(c->d_disks, c->slot_disk, c->N, c->key[0], c->val[0], c->rfix_longs, c->rfix_count);
+    k_rfix_long<<<(unsigned)std::max(1, std::min(c->n_sm_regrid, 1024)), kZoneThreads, kZoneSmemBitonicMax, st>>>(
+        c->d_disks, c->slot_disk, c->key[0], c->val[0], c->id[b], c->rfix_longs, c->rfix_count, c->rfix_count + 1);
     k_count_alive<<<(c->n_disks + 7) / 8, 256, 0, st>>>(c->d_disks, c->n_disks, c->key[0], c->n_alive, c->status);
     ZoneArgs A;
     A.params = c->d_params;
@@ -722,7 +879,7 @@ cudaError_t launch_regrid(mcd_ctx *c)
     k_dead_tail<<<gN, 256, 0, st>>>(c->d_disks, c->slot_disk, c->N, c->n_alive, c->val[0], c->m[b], c->M[b], c->r[b],
                                     c->z[b], c->id[b], c->m[nb], c->M[nb], c->r[nb], c->z[nb], c->id[nb],
                                     c->tracer ? c->q[b] : nullptr, c->tracer ? c->q[nb] : nullptr);
-    c->launches += 4 + 4 * kRadixPasses;
+    c->launches += 6 + 4 * kRadixUpperPasses;
     return cudaGetLastError();
 }
 
