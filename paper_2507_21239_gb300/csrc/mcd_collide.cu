@@ -4,7 +4,8 @@
 // themselves are in mcd_collide.cuh, instantiated per (precision, swarms per
 // thread, exact total) in mcd_collide_f32s1.cu, mcd_collide_f32s2.cu,
 // mcd_collide_f32s1x.cu, mcd_collide_f32s2x.cu and mcd_collide_f64.cu, and the
-// control-warp variants in mcd_collide_ws.cuh (mcd_collide_f32ws.cu).
+// control-warp variants in mcd_collide_ws.cuh (mcd_collide_f32ws4.cu,
+// mcd_collide_f32ws10.cu).
 #include <algorithm>
 
 #include "mcd_collide_ws.cuh"
