@@ -273,10 +273,10 @@ int mcd_get_total_rates(mcd_ctx *ctx, int32_t disk, double *Rtot, int32_t where)
 
 /*
  * The collide's cell classes (disks grouped by particles per cell) and the
- * variant each runs: threads per cell, swarms per thread, dv-matrix store,
- * and the timed trial's candidates (the time per event of each, the median
- * of three runs of kTrialEvents = 256 events on up to 8 of the class's
- * largest cells).  Host memory; up to cap records, *count the number of
+ * variant each runs: threads per cell, swarms per thread, control warp,
+ * dv-matrix store, and the timed trial's candidates (the time per event of
+ * each, the median of five runs of 512 events on up to 8 of the class's
+ * largest cells, after one warm-up run).  Host memory; up to cap records, *count the number of
  * classes.  This is the implementation's scheduling, not the paper's method.
  */
 #define MCD_MAX_TRIALS 12

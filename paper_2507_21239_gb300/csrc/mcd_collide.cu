@@ -493,14 +493,14 @@ cudaError_t launch_collide_impl(mcd_ctx *cx, int from_state, double t_end)
 
 // ---- the timed trial ---------------------------------------------------------------------
 // For every class with more than one candidate (swarms per thread 1 or 2 where
-// 2 takes fewer warps; the shared, workspace or no matrix), up to 8 of the
-// class's largest cells run kTrialEvents events each from the current masses,
-// into scratch copies (the particle and tracer buffers the next regrid
-// overwrites, the row-sum dump and a scratch status), once to warm up and
-// three times timed with CUDA events; the candidate with the smallest median
-// time is kept.  The state of the context does not change.  The options MCD_OPT_SWARMS_PER_THREAD
+// 2 takes fewer warps, or the control warp; the shared, workspace or no
+// matrix), up to 8 of the class's largest cells run kTrialEvents events each
+// from the current masses, into scratch copies (the particle and tracer
+// buffers the next regrid overwrites, the row-sum dump and a scratch status),
+// once to warm up and kTrialRuns times timed with CUDA events; the candidate
+// with the smallest median time is kept.  The state of the context does not change.  The options MCD_OPT_SWARMS_PER_THREAD
 // and MCD_OPT_DV_MATRIX, when set, take the choice out of the trial.
-constexpr int kTrialEvents = 256, kTrialCells = 8;
+constexpr int kTrialEvents = 512, kTrialCells = 8, kTrialRuns = 5;
 
 template <class T>
 static cudaError_t tune_impl(mcd_ctx *c)
@@ -584,8 +584,8 @@ static cudaError_t tune_impl(mcd_ctx *c)
             if (L.S != cs.S || L.store != cs.store) continue;  // (the launch would not run this candidate)
             if (L.smem > (size_t)c->smem_optin) continue;
             A.dvg = L.store == 2 ? k.dvg : nullptr;
-            float ms[4] = {};
-            for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+            float ms[kTrialRuns + 1] = {};
+            for (int rep = 0; rep <= kTrialRuns && e == cudaSuccess; ++rep) {
                 e = cudaMemcpyAsync(A.m, c->m[b], 8 * c->N, cudaMemcpyDeviceToDevice, st);
                 if (e == cudaSuccess && A.q) e = cudaMemcpyAsync(A.q, c->q[b], 8 * c->N, cudaMemcpyDeviceToDevice, st);
                 if (e == cudaSuccess) e = cudaEventRecord(t0, st);
@@ -598,8 +598,8 @@ static cudaError_t tune_impl(mcd_ctx *c)
                 if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[rep], t0, t1);
             }
             if (e != cudaSuccess) break;
-            std::sort(ms + 1, ms + 4);
-            const float us = 1e3f * ms[2] / kTrialEvents;
+            std::sort(ms + 1, ms + kTrialRuns + 1);
+            const float us = 1e3f * ms[1 + kTrialRuns / 2] / kTrialEvents;
             if (k.n_trials < kMaxTrials) {
                 k.trial_us[k.n_trials] = us;
                 k.trial_S[k.n_trials] = cs.S;

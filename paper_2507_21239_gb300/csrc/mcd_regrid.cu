@@ -271,39 +271,6 @@ __global__ void __launch_bounds__(kRadixThreads, 2) k_radix_scatter(const DiskDe
     }
 }
 
-// the first position of each disk's sorted keys that holds +inf (a removed
-// particle): one warp per disk, a 32-way search (each round narrows [lo, hi)
-// to one of 32 sub-ranges with one load per lane), so the dependent loads are
-// log32 of the disk's size rather than log2
-__global__ void k_count_alive(const DiskDev *disks, int nd, const uint64_t *key, int64_t *n_alive, int32_t *status)
-{
-    const int d = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (d >= nd) return;
-    const DiskDev D = disks[d];
-    const uint64_t *k = key + D.p_off;
-    int64_t lo = 0, hi = D.n0;  // the answer lies in [lo, hi]: keys below lo are finite, from hi on +inf
-    while (hi - lo > 0) {
-        // lane l probes position lo + (l + 1) * ceil((hi - lo) / 32) - 1 (the last of its sub-range)
-        const int64_t step = (hi - lo + 31) >> 5;
-        const int64_t p = lo + (int64_t)(lane + 1) * step - 1;
-        const bool inf = p < hi && !(k[p] < kInfKey);
-        const unsigned b = __ballot_sync(0xffffffffu, inf);
-        if (b == 0u) {
-            lo += ((hi - lo) / step) * step;  // every probed key finite: one past the last probe below hi
-        } else {
-            const int f = __ffs(b) - 1;  // the first sub-range whose last key is +inf
-            const int64_t nlo = lo + (int64_t)f * step, nhi = lo + (int64_t)(f + 1) * step - 1;
-            lo = nlo;
-            hi = nhi;  // the answer is in [nlo, nhi]: position nhi is +inf
-            if (step == 1) break;
-        }
-    }
-    if (lane == 0) {
-        n_alive[d] = lo;
-        if (lo == 0 && D.n0 > 0) atomicOr(status, kStEmpty);
-    }
-}
-
 // a zone element in shared memory: (z key lo, z key hi, id, source slot)
 __device__ __forceinline__ uint64_t el_key(const uint4 &e) { return ((uint64_t)e.y << 32) | e.x; }
 __device__ __forceinline__ bool zless(const uint4 &a, const uint4 &b)
@@ -376,12 +343,21 @@ constexpr int kZoneThreads = 512;  // two zones per SM
 constexpr int kRunShort = kRunShortMax;
 
 __global__ void k_rfix(const DiskDev *disks, const int32_t *slot_disk, int64_t N, uint64_t *key, uint32_t *val,
-                       int64_t *longs, int32_t *n_long)
+                       int64_t *longs, int32_t *n_long, int64_t *n_alive, int32_t *status)
 {
     const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= N) return;
-    const DiskDev D = disks[slot_disk[s]];
+    const int d = slot_disk[s];
+    const DiskDev D = disks[d];
     const int64_t end = D.p_off + D.n0;
+    // the disk's live count: the last finite key's position + 1 (removed particles, +inf, sort last; a run
+    // never mixes finite and +inf keys, so the fix-up below does not move this boundary)
+    const bool fin = key[s] < kInfKey;
+    if (fin && (s + 1 == end || !(key[s + 1] < kInfKey))) n_alive[d] = s + 1 - D.p_off;
+    if (!fin && s == D.p_off) {
+        n_alive[d] = 0;
+        atomicOr(status, kStEmpty);
+    }
     const uint32_t hi = (uint32_t)(key[s] >> 32);
     if (hi == (uint32_t)(kInfKey >> 32)) return;
     if (s + 1 >= end || (uint32_t)(key[s + 1] >> 32) != hi) return;
@@ -849,10 +825,10 @@ cudaError_t launch_regrid(mcd_ctx *c)
     // runs of equal upper words into (key, id) order
     cudaError_t e = cudaMemsetAsync(c->rfix_count, 0, 2 * sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
-    k_rfix<<<gN, 256, 0, st>>>(c->d_disks, c->slot_disk, c->N, c->key[0], c->val[0], c->rfix_longs, c->rfix_count);
+    k_rfix<<<gN, 256, 0, st>>>(c->d_disks, c->slot_disk, c->N, c->key[0], c->val[0], c->rfix_longs, c->rfix_count,
+                               c->n_alive, c->status);
     k_rfix_long<<<(unsigned)std::max(1, std::min(c->n_sm_regrid, 1024)), kZoneThreads, kZoneSmemBitonicMax, st>>>(
         c->d_disks, c->slot_disk, c->key[0], c->val[0], c->id[b], c->rfix_longs, c->rfix_count, c->rfix_count + 1);
-    k_count_alive<<<(c->n_disks + 7) / 8, 256, 0, st>>>(c->d_disks, c->n_disks, c->key[0], c->n_alive, c->status);
     ZoneArgs A;
     A.params = c->d_params;
     A.disks = c->d_disks;
@@ -879,7 +855,7 @@ cudaError_t launch_regrid(mcd_ctx *c)
     k_dead_tail<<<gN, 256, 0, st>>>(c->d_disks, c->slot_disk, c->N, c->n_alive, c->val[0], c->m[b], c->M[b], c->r[b],
                                     c->z[b], c->id[b], c->m[nb], c->M[nb], c->r[nb], c->z[nb], c->id[nb],
                                     c->tracer ? c->q[b] : nullptr, c->tracer ? c->q[nb] : nullptr);
-    c->launches += 6 + 4 * kRadixUpperPasses;
+    c->launches += 5 + 4 * kRadixUpperPasses;
     return cudaGetLastError();
 }
 
