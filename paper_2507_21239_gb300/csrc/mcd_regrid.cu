@@ -488,10 +488,12 @@ __device__ __forceinline__ int zdigit(const uint4 &e, int p, int id_passes, int 
                          : (int)((el_key(e) >> (8 * (zb0 + p - id_passes))) & 255u);
 }
 
-// Stable LSD radix sort of a[0, n) by (z key, id): the id's bytes first, then
-// the z key's, so elements equal in z end in id order.  Each pass ranks a
-// warp's items with a warp match (item order it, lane within a warp; warps in
-// order), offsets every (warp, digit) run and scatters into the other buffer.
+// Stable LSD radix sort of a[0, n): id_passes passes over the id's bytes,
+// then the z key's bytes from byte zb0 up (zb0 = 0 and all id bytes: by
+// (z key, id); zb0 = 4 and no id pass: by the key's upper word, stably).
+// Each pass ranks a warp's items by ballots (item order it, lane within a
+// warp; warps in order), offsets every (warp, digit) run and scatters into the
+// other buffer.
 // Returns the buffer that holds the result.  n <= kZoneRadixMax.  The
 // counters live in the radix path's own part of the dynamic shared memory
 // (kZoneRadixScratch bytes after the two buffers), so the bitonic path keeps
