@@ -307,6 +307,25 @@ int mcd_get_event_log(mcd_ctx *ctx, int32_t *ijo, double *t, double *m_new, int6
 
 int mcd_get_stats(mcd_ctx *ctx, int32_t disk, mcd_stats *out);
 
+/*
+ * Checkpoint and resume (the paper describes none; the random streams are
+ * keyed by (seed, disk) and counted by step, cell and event or particle id,
+ * so a resumed run repeats the checkpointed one bit for bit).  mcd_set_clock
+ * sets the context's clock t [s] and its step counter; mcd_set_counters sets
+ * a disk's collision-event count and accreted swarm mass [g], as
+ * mcd_get_stats read them from the checkpointed context.  To resume, create a
+ * context with the same parameters, grids, seed and precision, then call
+ * mcd_set_particles (and mcd_set_tracer, mcd_set_gas_table and the options
+ * the checkpointed context had) for every disk, mcd_set_clock once and
+ * mcd_set_counters per disk.  On MCD_MIXED the collide variant must be the
+ * same one (pin MCD_OPT_SWARMS_PER_THREAD, or MCD_OPT_CONTROL_WARP): the
+ * variants' choice scans sum in different orders.  Asynchronous (the values
+ * reach the device as kernel arguments); MCD_EINVAL for a non-finite or
+ * negative time, a negative step or count, or a bad disk.
+ */
+int mcd_set_clock(mcd_ctx *ctx, double t, int64_t step);
+int mcd_set_counters(mcd_ctx *ctx, int32_t disk, int64_t events, double accreted_mass);
+
 /* Diagnostics (Benchmark section: the dust surface density as a function of
  * particle mass and distance from the star, here summarised per radial bin).
  * For every bin b = [edges[b], edges[b+1]) of disk `disk`, over the particles

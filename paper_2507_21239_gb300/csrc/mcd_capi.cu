@@ -857,6 +857,42 @@ int mcd_get_launch_count(mcd_ctx *c, int64_t *launches)
     return MCD_OK;
 }
 
+namespace {
+// the resumed clock, step counter and a disk's counters, passed by value
+__global__ void k_restore_clock(mcd::StepState *st, double t, int64_t step)
+{
+    st->t = t;
+    st->step = step;
+}
+__global__ void k_restore_counters(unsigned long long *events, double *accreted, unsigned long long ev, double acc)
+{
+    *events = ev;
+    *accreted = acc;
+}
+}  // namespace
+
+int mcd_set_clock(mcd_ctx *c, double t, int64_t step)
+{
+    if (!c || !isfinite(t) || t < 0.0 || step < 0) return MCD_EINVAL;
+    k_restore_clock<<<1, 1, 0, c->stream>>>(c->state, t, step);
+    c->launches += 1;
+    if (cudaGetLastError() != cudaSuccess) return MCD_ECUDA;
+    c->t_host = t;
+    c->t_known = true;
+    c->step_host = step;
+    return MCD_OK;
+}
+
+int mcd_set_counters(mcd_ctx *c, int32_t disk, int64_t events, double accreted_mass)
+{
+    if (!c || disk < 0 || disk >= c->n_disks || events < 0 || !isfinite(accreted_mass) || accreted_mass < 0.0)
+        return MCD_EINVAL;
+    k_restore_counters<<<1, 1, 0, c->stream>>>(c->events_total + disk, c->accreted + disk,
+                                                (unsigned long long)events, accreted_mass);
+    c->launches += 1;
+    return cudaGetLastError() == cudaSuccess ? MCD_OK : MCD_ECUDA;
+}
+
 int mcd_sync(mcd_ctx *c)
 {
     if (!c) return MCD_EINVAL;

@@ -102,6 +102,8 @@ def lib():
         L.mcd_get_cell_events.argtypes = [_vp, C.c_int32, _vp, C.c_int32]
         L.mcd_get_event_log.argtypes = [_vp, _vp, _vp, _vp, C.c_int64, _P(C.c_int64)]
         L.mcd_get_stats.argtypes = [_vp, C.c_int32, _P(mcd_stats)]
+        L.mcd_set_clock.argtypes = [_vp, C.c_double, C.c_int64]
+        L.mcd_set_counters.argtypes = [_vp, C.c_int32, C.c_int64, C.c_double]
         L.mcd_get_tracer.argtypes = [_vp, C.c_int32, _vp, C.c_int32]
         L.mcd_set_tracer.argtypes = [_vp, C.c_int32, _vp, C.c_int32]
         L.mcd_moments.argtypes = [_vp, C.c_int32, C.c_int32, _vp, _vp]
@@ -307,6 +309,14 @@ def mcd_get_tracer(ctx: int, disk: int, q, where: int = MCD_HOST):
 
 def mcd_set_tracer(ctx: int, disk: int, q, where: int = MCD_HOST):
     _check(lib().mcd_set_tracer(ctx, disk, _ptr(q), where), "mcd_set_tracer")
+
+
+def mcd_set_clock(ctx: int, t: float, step: int):
+    _check(lib().mcd_set_clock(ctx, t, step), "mcd_set_clock")
+
+
+def mcd_set_counters(ctx: int, disk: int, events: int, accreted_mass: float):
+    _check(lib().mcd_set_counters(ctx, disk, events, accreted_mass), "mcd_set_counters")
 
 
 def mcd_set_option(ctx: int, key: int, value: float):
