@@ -196,7 +196,10 @@ def test_total_rate_plain_and_compensated(spt):
     plain sum misses in most cells.  Both equal the oracle's FP64 total of the
     same cell to 1e-5.  spt 0: the control-warp variant, whose plain total is
     the one warp's scan of 16 row sums per lane (the exact total then runs the
-    block variant with its helper warp)."""
+    block variant with its helper warp).  The two runs' row sums agree bit for
+    bit when one kernel forms them and to 1e-6 across kernels (the compiler
+    may fuse a product into a sum in one kernel and not in another): each
+    total is checked against its own run's row sums."""
     P = W.benchmark_disk()
     grid = (2, 4, 400)
     N = grid[0] * grid[1] * grid[2]
@@ -211,8 +214,11 @@ def test_total_rate_plain_and_compensated(spt):
         mcd.mcd_set_particles(d.ctx, 0, m, p["M"], r, z, p["id"])
         mcd.mcd_regrid(d.ctx)
         shape = ((mcd.MCD_OPT_SWARMS_PER_THREAD, spt),) if spt else ((mcd.MCD_OPT_CONTROL_WARP, -1 if exact else 1),)
+        # (the row sums are formed from recomputed entries in every run: the
+        # stored-matrix build rounds a few entries differently, and a timed
+        # trial left free to pick the store would make the runs' rows differ)
         for key, v in ((mcd.MCD_OPT_MAX_EVENTS, 0), (mcd.MCD_OPT_CAP_STOPS, 1), (mcd.MCD_OPT_DUMP_R, 1),
-                       (mcd.MCD_OPT_EXACT_TOTAL, exact)) + shape:
+                       (mcd.MCD_OPT_EXACT_TOTAL, exact), (mcd.MCD_OPT_DV_MATRIX, 0)) + shape:
             mcd.mcd_set_option(d.ctx, key, v)
         mcd.mcd_collide(d.ctx, 1.0)
         assert mcd.mcd_sync(d.ctx) == mcd.MCD_OK
@@ -230,13 +236,18 @@ def test_total_rate_plain_and_compensated(spt):
     plain_misses = 0
     for c in range(grid[0] * grid[1]):
         Rc = R[off[c]:off[c + 1]]
-        assert len(Rc) == 400 and np.array_equal(Rc, out[0][0][off[c]:off[c + 1]])
-        exact = math.fsum(Rc)
-        plain = _plain_scan_total(Rc, spt if spt else 16)
+        R0 = out[0][0][off[c]:off[c + 1]]
+        assert len(Rc) == 400
+        if spt:
+            assert np.array_equal(Rc, R0)
+        else:
+            assert np.max(np.abs(Rc / R0 - 1)) <= 1e-6
+        exact, exact0 = math.fsum(Rc), math.fsum(R0)
+        plain = _plain_scan_total(R0, spt if spt else 16)
         assert out[0][1][c] == plain, (c, out[0][1][c], plain)  # the kernel's plain sum, bit for bit
-        assert abs(plain / exact - 1) <= 10 * 2.0**-24
+        assert abs(plain / exact0 - 1) <= 10 * 2.0**-24
         assert abs(out[1][1][c] / exact - 1) <= 2e-9, (c, out[1][1][c], exact)
-        plain_misses += abs(plain / exact - 1) > 2e-9
+        plain_misses += abs(plain / exact0 - 1) > 2e-9
         sl = slice(off[c], off[c + 1])
         _, Ro = oracle.rate_matrix(P, cb[c, 4], cb[c, 5], V[c], x["m"][sl], x["M"][sl])
         assert abs(out[1][1][c] / math.fsum(Ro) - 1) < 1e-5
