@@ -618,7 +618,7 @@ int mcd_set_particles(mcd_ctx *c, int32_t disk, const double *m, const double *M
     cp(c->r[sb] + o, r, 8 * n);
     cp(c->z[sb] + o, z, 8 * n);
     cp(c->id[sb] + o, id, 4 * n);
-    // the id counts go to the sort's value buffer, the verdict to its histogram
+    // the id counts go to the sort's value buffer, the check's result to its histogram
     // (both free between regrids)
     uint32_t *cnt = c->val[1] + o;
     int32_t *bad = reinterpret_cast<int32_t *>(c->hist);
