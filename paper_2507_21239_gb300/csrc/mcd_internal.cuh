@@ -211,7 +211,7 @@ struct StepState {
 constexpr int kRunShortMax = 64;
 
 // radix sort tile: 256 threads x 16 keys
-constexpr int kRadixThreads = 256, kRadixItems = 16, kRadixTile = kRadixThreads * kRadixItems;
+constexpr int kRadixThreads = 256, kRadixItems = 8, kRadixTile = kRadixThreads * kRadixItems;
 constexpr int kRadixBins = 256, kRadixPasses = 8;
 constexpr int kRadixUpperPasses = 4;  // the r sort runs the passes of the keys' upper four bytes
 

@@ -170,8 +170,10 @@ constexpr size_t kScatterStage = (size_t)kRadixTile * (sizeof(uint64_t) + sizeof
 // One tile: rank every key within its digit (warp match, then a prefix over
 // warps), stage the tile in shared memory in digit order, and write it out
 // run by run, so consecutive threads store consecutive addresses of a digit's
-// destination range.
-__global__ void __launch_bounds__(kRadixThreads, 2) k_radix_scatter(const DiskDev *disks, const int32_t *tile_disk,
+// destination range.  Tiles of 2,048 keys and four resident CTAs per SM (64
+// registers): a disk's tiles spread over the SMs in one wave with little
+// imbalance between SMs.
+__global__ void __launch_bounds__(kRadixThreads, 4) k_radix_scatter(const DiskDev *disks, const int32_t *tile_disk,
                                                                  const uint64_t *ksrc, const uint32_t *vsrc,
                                                                  uint64_t *kdst, uint32_t *vdst, int shift,
                                                                  const uint32_t *hist, const uint32_t *part)
